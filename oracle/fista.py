@@ -1,0 +1,86 @@
+"""Sparse AAHRT solve of the oracle (Sec. 4, eqs. cost1, ISTA and soft).
+
+    minimise  1/2 ||d - L m||_2^2 + lambda ||m||_1                 (eq. cost1)
+
+by forward-backward splitting (eq. ISTA)
+
+    m^{k+1} = soft(m^k + gamma L^T (d - L m^k), gamma*lambda)
+
+with the soft shrinkage of eq. soft, soft(x, t) = x * max(1 - t/|x|, 0).
+With momentum on, the gradient step is taken at the extrapolated point z^k
+of Beck and Teboulle's FISTA:
+
+    m^{k+1} = soft(z^k + gamma L^T (d - L z^k), gamma*lambda)
+    t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2
+    z^{k+1} = m^{k+1} + ((t_k - 1)/t_{k+1}) (m^{k+1} - m^k)
+
+starting from m^0 = z^0 = 0 (or a given m^0 = z^0) and t_0 = 1.  The paper
+does not give gamma; gamma = 0.95 / sigma^2 with sigma^2 estimated by power
+iteration on L^T L started from L^T d.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import ops
+
+
+def soft(x, t):
+    """Soft shrinkage of eq. soft: x * max(1 - t/|x|, 0) (0 at x = 0)."""
+    ax = np.abs(x)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        scale = np.where(ax > 0.0, np.maximum(1.0 - t / ax, 0.0), 0.0)
+    return x * scale
+
+
+def momentum_schedule(iters: int):
+    """FISTA extrapolation weights beta_k = (t_k - 1)/t_{k+1}, k < iters."""
+    t = 1.0
+    out = []
+    for _ in range(iters):
+        tn = 0.5 * (1.0 + np.sqrt(1.0 + 4.0 * t * t))
+        out.append((t - 1.0) / tn)
+        t = tn
+    return np.array(out)
+
+
+def power_sigma2(plan, d, iters: int = 30, impl: str = "c") -> float:
+    """Estimate of the largest eigenvalue of L^T L by power iteration from
+    L^T d / ||L^T d|| (Rayleigh quotient of the last iterate)."""
+    v = ops.adjoint(plan, d, impl)
+    v = v / np.linalg.norm(v)
+    lam = 0.0
+    for _ in range(iters):
+        w = ops.adjoint(plan, ops.forward(plan, v, impl), impl)
+        lam = float(np.vdot(v, w).real)
+        v = w / np.linalg.norm(w)
+    return lam
+
+
+def objective(plan, d, m, lam, impl: str = "c") -> float:
+    r = d - ops.forward(plan, m, impl)
+    return 0.5 * float(np.sum(r * r)) + lam * float(np.sum(np.abs(m)))
+
+
+def solve(plan, d, lam, iters, gamma, momentum: bool = True, m0=None,
+          impl: str = "c", history: bool = False):
+    """Run `iters` iterations of ISTA (momentum off) or FISTA (on)."""
+    d = np.asarray(d, np.float64)
+    shape = (plan.ntau, plan.nq, plan.ntheta)
+    m = np.zeros(shape) if m0 is None else np.array(m0, np.float64)
+    z = m.copy()
+    t = 1.0
+    hist = []
+    for _ in range(iters):
+        g = ops.adjoint(plan, d - ops.forward(plan, z, impl), impl)
+        m_new = soft(z + gamma * g, gamma * lam)
+        if momentum:
+            tn = 0.5 * (1.0 + np.sqrt(1.0 + 4.0 * t * t))
+            z = m_new + ((t - 1.0) / tn) * (m_new - m)
+            t = tn
+        else:
+            z = m_new
+        m = m_new
+        if history:
+            hist.append(objective(plan, d, m, lam, impl))
+    return (m, hist) if history else m
