@@ -1,0 +1,422 @@
+#!/usr/bin/env python3
+"""Throughput of the AAHRT operator pair inside the FISTA sparse solve.
+
+One step = one sparse solve (100 FISTA iterations; each iteration is one
+forward + adjoint pair with the residual and the shrinkage/momentum update
+fused) of the paper-scale gather: nt = 1001 at 4 ms, 2000 traces uniform in
+a 3 km disc, 100 curvatures x 36 azimuths, 30 Ricker events + 10% noise
+(synthetic, seeded).  value = pairs/s over the whole job; gathers/s is the
+same rate per 100-iteration solve.  Inputs are resident in HBM for `value`;
+`e2e` passes pinned host buffers to the C ABI so the host<->device copies
+of d and m are inside the timed region.  L2 is flushed (256 MB write)
+between timed steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank runs an independent replica on its own GPU (the
+path needs no communication); rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("AAHRT fwd+adj pairs/s and FISTA gathers/s on 1 GB300, %HBM roofline, "
+          "err vs FP64")
+ITERS = 100
+WORKLOAD = ("paper-scale gather: nt=1001 dt=4ms, 2000 traces in a 3 km disc, "
+            "100 q x 36 azimuths; one step = one 100-iteration FISTA solve")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    mhz.append(float(parts[1]))
+                    mx = float(parts[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not mhz:
+            return None
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": mx, "samples": len(mhz),
+                "reasons": sorted(reasons)}
+
+
+def stage_bytes(info):
+    """Algorithmic bytes per launch of each stage inside a FISTA iteration:
+    each stage reads its input once and writes its output once."""
+    m, d = 4 * info.model_len, 4 * info.data_len
+    x, y = 8 * info.xspec_len, 8 * info.yspec_len
+    return [m + x,            # 0 stretch + FFT (model side)
+            x + y,            # 1 slice forward
+            y + 2 * d,        # 2 inverse FFT + unstretch, residual d - Lz fused
+            d + y,            # 3 unstretch^T + FFT (data side)
+            y + x,            # 4 slice adjoint
+            x + 4 * m,        # 5 inverse FFT + stretch^T, FISTA update fused (m, z in/out)
+            0]
+
+
+def traffic_record(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path))
+        h = hashlib.sha256()
+        csrc = os.path.join(ROOT, "paper_2505_00387_gb300", "csrc")
+        for f in sorted(os.listdir(csrc)):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+        if rec.get("csrc_sha256") != h.hexdigest():
+            return None
+        return rec.get("kernels", {}).get(kernel)
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------ ours
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_info()
+    if world > 1:
+        dist.init_process_group(backend="nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2505_00387_gb300 import build as B
+    if rank == 0 or world == 1:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2505_00387_gb300 import _lib as L
+    from paper_2505_00387_gb300 import synthetic as syn
+    from paper_2505_00387_gb300.plan import AahrtPlan
+
+    g = syn.config1(seed=1 + rank)
+    gp = AahrtPlan(**g.geom_kwargs())
+    info = gp.info
+    d = torch.from_numpy(g.d.astype(np.float32).ravel()).to(dev)
+    m = torch.zeros(gp.model_len, device=dev)
+    stream = torch.cuda.current_stream()
+
+    # step length and lambda = 0.05 max|L^T d| from the device (setup, untimed)
+    _, si = gp.sparse_solve(d, 0.0, 0, m, lambda_rel=0.05, power_iters=30)
+    lam, gamma = float(getattr(si, "lambda")), float(si.gamma)
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, device=dev)
+
+    def step():
+        gp.sparse_solve(d, lam, ITERS, m, gamma=gamma, use_graph=True, want_info=False)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    def timed(fn, k, profile=False):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(k)]
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for i in range(k):
+            flush.zero_()
+            ev[i][0].record(stream)
+            fn()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        return sum(a.elapsed_time(b) for a, b in ev)
+
+    t_launch0 = gp.stage_times()[1]
+    sampler = ClockSampler(local)
+    sampler.start()
+    total_ms = timed(step, args.steps)
+    clocks = sampler.stop()
+    t_launch1 = gp.stage_times()[1]
+    launches = int(sum(t_launch1[:6]) - sum(t_launch0[:6]))
+
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    pairs = args.steps * ITERS * world
+    value = pairs / (total_ms / 1e3)
+
+    # end to end: pinned host d in, pinned host m out, through the C ABI
+    d_host = torch.from_numpy(g.d.astype(np.float32).ravel()).pin_memory()
+    m_host = torch.zeros(gp.model_len, dtype=torch.float32).pin_memory()
+    o = L.aahrt_solve_opts(0, 0, 0, 1, gamma, 0.0)
+
+    def step_e2e():
+        L.aahrt_sparse_solve(gp.handle, d_host.data_ptr(), lam, ITERS, m_host.data_ptr(), o,
+                             False, int(stream.cuda_stream))
+
+    step_e2e()
+    torch.cuda.synchronize()
+    e2e_ms = timed(step_e2e, args.steps)
+    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = pairs / (float(te.item()) / 1e3)
+
+    # per-stage device time over the same kind of steps (eager launches,
+    # CUDA events around every stage on the launching stream)
+    gp.set_profiling(True)
+    for _ in range(args.steps):
+        flush.zero_()
+        gp.sparse_solve(d, lam, ITERS, m, gamma=gamma, use_graph=False, want_info=False)
+    torch.cuda.synchronize()
+    st_ms, st_n = gp.stage_times()
+    gp.set_profiling(False)
+
+    if world > 1:
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+
+    sb = stage_bytes(info)
+    names = L.STAGE_NAMES
+    per_launch = [st_ms[i] / st_n[i] if st_n[i] else 0.0 for i in range(L.AAHRT_NSTAGES)]
+    top = max(range(6), key=lambda i: st_ms[i])
+    peak, peak_kind = peaks()
+    achieved = sb[top] / (per_launch[top] * 1e-3) / 1e9
+    iter_ms = sum(st_ms[:6]) / (args.steps * ITERS)
+    iter_bytes = sum(sb[:6])
+    kernel_names = ["r2c_kernel", "slice_fwd_kernel", "c2r_kernel", "r2c_kernel",
+                    "slice_adj_kernel", "c2r_kernel"]
+    tr = traffic_record(names[top])
+    line = {
+        "metric": METRIC,
+        "value": round(value, 3),
+        "unit": "pairs/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": max(args.warmup, 3),
+        "ms_per_step": round(total_ms / args.steps, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nt": g.nt, "dt": g.dt, "ntr": g.ntr, "nq": g.nq,
+                   "ntheta": g.ntheta, "fista_iters_per_step": ITERS, "nfft": info.nfft,
+                   "nbins": info.nbins, "spread_width": info.spread_width,
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "gathers_per_s": round(value / ITERS, 4),
+        "e2e": {"value": round(e2e_value, 3), "unit": "pairs/s",
+                "h2d_bytes_per_step": 4 * gp.data_len, "d2h_bytes_per_step": 4 * gp.model_len},
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": tr, "kernel": kernel_names[top], "stage": names[top],
+                     "bytes_per_launch": sb[top],
+                     "avg_launch_ms": round(per_launch[top], 5),
+                     "peak_source": peak_kind},
+        "pair_hbm": {"algorithmic_bytes_per_iteration": iter_bytes,
+                     "ms_per_iteration": round(iter_ms, 5),
+                     "achieved_GBps": round(iter_bytes / (iter_ms * 1e-3) / 1e9, 1),
+                     "frac_of_peak": round(iter_bytes / (iter_ms * 1e-3) / 1e9 / peak, 4)},
+        "stages": {names[i]: {"ms_per_launch": round(per_launch[i], 5),
+                              "launches": int(st_n[i]), "bytes_per_launch": sb[i],
+                              "GBps": round(sb[i] / (per_launch[i] * 1e-3) / 1e9, 1)
+                              if per_launch[i] else None}
+                   for i in range(L.AAHRT_NSTAGES) if st_n[i]},
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"], line["err_vs_fp64"] = cpu_baseline(g, gp, d, dev)
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(g, gp, d_dev, dev, pairs=2):
+    """The FP64 checker timed on this host's cores on a bounded sample of the
+    same workload (`pairs` forward+adjoint pairs of the full gather), and
+    the GPU path's relative error against those FP64 results."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from oracle import ops
+
+    p = oracle.make_plan(**g.geom_kwargs())
+    rng = np.random.default_rng(123)
+    mr = rng.standard_normal((g.ntau, g.nq, g.ntheta)).astype(np.float32).astype(np.float64)
+    ops.slice_forward(p.subset_traces([0]), np.zeros((p.nbins, p.nq, p.ntheta), complex))
+    t0 = time.perf_counter()
+    for _ in range(pairs):
+        d_or = ops.forward(p, mr)
+        m_or = ops.adjoint(p, g.d)
+    el = time.perf_counter() - t0
+    d_gpu = gp.forward(torch.from_numpy(mr.astype(np.float32).ravel()).to(dev))
+    m_gpu = gp.adjoint(d_dev)
+    d_gpu = d_gpu.cpu().numpy().astype(np.float64).reshape(d_or.shape)
+    m_gpu = m_gpu.cpu().numpy().astype(np.float64).reshape(m_or.shape)
+    err = {"forward_rel_l2": float(np.linalg.norm(d_gpu - d_or) / np.linalg.norm(d_or)),
+           "adjoint_rel_l2": float(np.linalg.norm(m_gpu - m_or) / np.linalg.norm(m_or))}
+    cb = {"value": round(pairs / el, 5), "unit": "pairs/s", "cores": ops.threads(),
+          "kind": "oracle",
+          "sample": f"{pairs} forward+adjoint pairs of the full gather, FP64, "
+                    f"{el:.1f} s wall"}
+    return cb, err
+
+
+# ------------------------------------------------------------- reference
+def run_reference(args):
+    """The FP64 checker on the host cores, on the same workload and metric:
+    each step is a bounded sample (a fraction of the frequency bins of one
+    forward+adjoint pair), counted as that fraction of a pair."""
+    rank, world, local = dist_info()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from oracle import ops
+    from paper_2505_00387_gb300 import synthetic as syn
+
+    g = syn.config1(seed=1)
+    p = oracle.make_plan(**g.geom_kwargs())
+    nsteps = args.steps + max(args.warmup, 3)
+    frac = min(1.0, 12.0 / nsteps)
+    nb = max(1, int(round(p.nbins * frac)))
+    frac = nb / p.nbins
+    rng = np.random.default_rng(123)
+    m = rng.standard_normal((g.ntau, g.nq, g.ntheta))
+    ps = p
+
+    def step():
+        X = ops.rfft_bins(ps, ops.stretch(ps, m.reshape(ps.ntau, -1))).reshape(
+            ps.nbins, ps.nq, ps.ntheta)
+        from dataclasses import replace
+        sub = replace(ps, kmax=nb - 1)
+        Y = ops.slice_forward(sub, np.ascontiguousarray(X[:nb]))
+        full = np.zeros((ps.nbins, ps.ntr), complex)
+        full[:nb] = Y
+        dd = ops.unstretch(ps, ops.irfft_bins(ps, full))
+        R = ops.irfft_bins_T(ps, ops.unstretch_T(ps, dd))
+        Xa = ops.slice_adjoint(sub, np.ascontiguousarray(R[:nb]))
+        fullx = np.zeros((ps.nbins, ps.nq * ps.ntheta), complex)
+        fullx[:nb] = Xa.reshape(nb, -1)
+        ops.stretch_T(ps, ops.rfft_bins_T(ps, fullx))
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    el = time.perf_counter() - t0
+    value = args.steps * frac / el
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": round(value, 6),
+        "unit": "pairs/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": max(args.warmup, 3),
+        "ms_per_step": round(el / args.steps * 1e3, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nt": g.nt, "dt": g.dt, "ntr": g.ntr, "nq": g.nq,
+                   "ntheta": g.ntheta, "fista_iters_per_step": ITERS, "nfft": p.nfft,
+                   "nbins": p.nbins, "parallelism": "host cores"},
+        "cpu_baseline": {"value": round(value, 6), "unit": "pairs/s", "cores": ops.threads(),
+                         "kind": "oracle",
+                         "sample": f"per step {nb} of {p.nbins} frequency bins of one "
+                                   f"forward+adjoint pair (= {frac:.3f} pair), FP64"},
+        "e2e": {"value": round(value, 6), "unit": "pairs/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

@@ -1,0 +1,226 @@
+/*
+ * aahrt.h -- C ABI of the GB300 azimuthally anisotropic hyperbolic Radon
+ * transform (AAHRT) library, libaahrt.so.
+ *
+ * The operator (Sec. 3 of Mokhtari & Gholami, "Fast Azimuthally Anisotropic
+ * 3D Radon Transform by Generalized Fourier Slice Theorem"):
+ *
+ *   d = L m,   L = S^{-1} F1^{-1} P F2 S                       (eq. axb2)
+ *
+ * maps a Radon model m(tau, q, theta) -- intercept time, curvature
+ * q = squared slowness, azimuth -- to a CMP cube d(t, trace) through the
+ * hyperbolic basis of eq. Inverse, computed by Algorithm 1 (time stretch
+ * t' = t^2, FFT, Fourier slice k_q = f' r^2 / theta = atan(y/x) of eq.
+ * inv_GFST, inverse FFT, stretch undone).  aahrt_adjoint applies the exact
+ * transpose L^T (the velocity stack of Sec. 3.2 / Algorithm 2, built as a
+ * true transpose of every stage) and aahrt_sparse_solve minimises
+ * 1/2||d - L m||^2 + lambda ||m||_1 (eq. cost1) by forward-backward splitting
+ * (eq. ISTA with the shrinkage of eq. soft), optionally with FISTA momentum.
+ *
+ * Discretisation (fixed at plan creation):
+ *   tau_i = i*dt (i < ntau), t_i = i*dt (i < nt), q_l = q0 + l*dq (l < nq),
+ *   theta_j = j*pi/ntheta (j < ntheta); a trace at offset (hx, hy) has
+ *   r^2 = hx^2 + hy^2 and axial azimuth atan2(hy, hx) mod pi, and reads the
+ *   two neighbouring azimuth slices with linear weights (theta factors of
+ *   eq. thli).  Stretched time is sampled inside an FFT frame of Nfft samples
+ *   (Nfft = power of two >= sigma_t*nt*(1+rho), rho = |q|max r^2max/tmax^2),
+ *   bins 0..K (K = Nfft/2-1, Nyquist excluded).  The DFT along q read at the
+ *   non-uniform k_q is evaluated by an exponential-of-semicircle spreading
+ *   kernel of `spread_width` taps on a 2x-or-more oversampled q grid (the
+ *   paper's step 3 uses linear interpolation; this is its accurate form).
+ *
+ * Memory layout (all float32, caller-owned):
+ *   model  m[g][tau][q][theta]   theta fastest, g = gather (ngather > 1) or
+ *                                cube (batched plans), each block contiguous
+ *   data   d[g][t][trace]        trace fastest
+ * The model and data buffers of aahrt_forward, aahrt_adjoint and
+ * aahrt_sparse_solve may be device memory (16-byte aligned) or host memory
+ * (pinned or pageable, 4-byte aligned); host buffers are copied through
+ * device staging buffers the plan allocates on first use, inside the call's
+ * stream order (with pageable memory the copies synchronise the host).
+ * Spectra of aahrt_apply_stage must be device memory.  Buffers of one call
+ * must not overlap.  Every call is stream-ordered on `stream` (a
+ * cudaStream_t; NULL is the legacy default stream) and returns without
+ * synchronising, except where stated.  The plan's workspace is reused by
+ * every call: calls on one plan must be serialised on one stream (or
+ * ordered by the caller).
+ *
+ * Errors: every int-returning function returns AAHRT_OK (0) or a negative
+ * AAHRT_ERR_* code; no function exits, throws or traps.  The text of the
+ * most recent error of the calling thread is aahrt_last_error().
+ */
+#ifndef AAHRT_H
+#define AAHRT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status */
+#define AAHRT_OK 0
+#define AAHRT_ERR_INVALID_ARG -1   /* bad size, pointer, alignment or option */
+#define AAHRT_ERR_OOM -2           /* device or host allocation failed */
+#define AAHRT_ERR_CUDA -3          /* a CUDA runtime call or launch failed */
+#define AAHRT_ERR_UNSUPPORTED -4   /* valid request this build cannot serve */
+#define AAHRT_ERR_TIMEOUT -5       /* a bounded device wait ran out */
+#define AAHRT_ERR_NONFINITE -6     /* NaN/Inf met where a finite value is needed */
+
+#define AAHRT_INTERP_KEYS 0        /* Keys cubic convolution, a = -1/2 (default) */
+#define AAHRT_INTERP_LINEAR 1      /* linear interpolation */
+
+typedef struct aahrt_plan aahrt_plan;
+
+/* Axes and trace geometry of one CMP cube.  hx, hy: host arrays of ntr
+ * offsets in metres, copied at plan creation (the caller keeps ownership).
+ * dt in seconds, q0 and dq in s^2/m^2.  Requires nt >= 4, ntau >= 4,
+ * nq >= 1, ntheta >= 1, ntr >= 1, dt > 0, dq > 0 when nq > 1, and at least
+ * one nonzero offset. */
+typedef struct {
+    int nt;
+    double dt;
+    int ntau;
+    int nq;
+    double q0;
+    double dq;
+    int ntheta;
+    int ntr;
+    const double *hx;
+    const double *hy;
+} aahrt_geom;
+
+/* Options; a zero-initialised struct selects every default. */
+typedef struct {
+    int interp_kind;    /* AAHRT_INTERP_KEYS (0) or AAHRT_INTERP_LINEAR */
+    int spread_width;   /* q-spreading kernel taps, 4..12; 0 = 7 */
+    int theta_group;    /* azimuth slices per slice-kernel block; 0 = automatic */
+    int ngather;        /* gathers sharing this geometry; 0 = 1 */
+    double sigma_t;     /* FFT frame oversampling of the time axis; 0 = 2 */
+    double fmax;        /* highest kept stretched frequency in 1/s^2; 0 = all */
+} aahrt_opts;
+
+/* What a plan chose (filled by aahrt_plan_query). */
+typedef struct {
+    int nfft;           /* FFT frame length along stretched time */
+    int ns;             /* stretched samples s_n = n*ds, n < ns */
+    int nbins;          /* kept frequency bins K+1 */
+    int nq_os;          /* oversampled q grid of the spreading kernel */
+    int spread_width;
+    int theta_group;
+    int ncube;          /* cubes of a batched plan (1 otherwise) */
+    int ngather;
+    double ds;          /* stretched sampling interval, s^2 */
+    double rho;         /* |q|max r^2max / tmax^2 */
+    double beta;        /* spreading kernel shape parameter */
+    long long model_len;     /* floats of one m buffer (all gathers/cubes) */
+    long long data_len;      /* floats of one d buffer */
+    long long xspec_len;     /* complex values of a model spectrum X[g][k][q][theta] */
+    long long yspec_len;     /* complex values of a data spectrum Y[g][k][trace] */
+    long long workspace_bytes;
+} aahrt_plan_info;
+
+/* Create a plan on the current CUDA device: validates the geometry,
+ * computes the stretched-time sampling (Sec. 3.3 steps 1-2) and the trace
+ * azimuth binning (eq. thli), and allocates the device workspace.  With
+ * opts->ngather = G > 1 the plan serves G gathers on this one geometry,
+ * stored back to back in m and d.  On success *out owns device memory until
+ * aahrt_plan_destroy. */
+int aahrt_plan_create(aahrt_plan **out, const aahrt_geom *geom,
+                      const aahrt_opts *opts);
+
+/* Create one plan for ncube independent CMP cubes of different fold and
+ * azimuth coverage.  All cubes must share nt, dt, ntau, nq, q0, dq and
+ * ntheta; they share one stretched-time sampling built from the largest
+ * offset of the whole batch.  m holds the cubes' models back to back,
+ * d their data back to back (cube c has geoms[c].ntr traces). */
+int aahrt_plan_create_batched(aahrt_plan **out, int ncube,
+                              const aahrt_geom *geoms, const aahrt_opts *opts);
+
+void aahrt_plan_destroy(aahrt_plan *plan);
+
+int aahrt_plan_query(const aahrt_plan *plan, aahrt_plan_info *info);
+
+/* d = L m (Algorithm 1; eq. axb2).  m: model_len floats, d: data_len floats,
+ * both device memory; d is overwritten. */
+int aahrt_forward(aahrt_plan *plan, const float *m, float *d, void *stream);
+
+/* m = L^T d, the exact transpose of aahrt_forward (Sec. 3.2 / Algorithm 2
+ * as a true adjoint).  m is overwritten. */
+int aahrt_adjoint(aahrt_plan *plan, const float *d, float *m, void *stream);
+
+/* One stage of the operator pair on caller buffers (for stage-by-stage
+ * checks and custom pipelines).  Spectra are interleaved complex float32
+ * (re, im), bins k = 0..nbins-1 with f_k = k/(nfft*ds):
+ *   stage 0  X = F S m          m (model_len) -> X (xspec_len), X[g][k][q][theta]
+ *   stage 1  Y = P X / nfft     X -> Y (yspec_len), Y[g][k][trace]  (Fourier slice)
+ *   stage 2  d = U H Y          Y -> d (data_len)
+ *   stage 3  Y = F U^T d        d -> Y
+ *   stage 4  X = P^H Y / nfft   Y -> X  (exact transpose of stage 1)
+ *   stage 5  m = S^T H X        X -> m
+ * F: DFT along stretched time (Alg. 1 step 2); H: band-limited Hermitian
+ * synthesis x_n = Re X_0 + 2 Re sum_{k>=1} X_k e^{+2 pi i k n/nfft} (so
+ * H/nfft is the paper's F1^{-1}, step 4); S, U: the stretch and its undoing
+ * (steps 1 and 5).  forward = 2 o 1 o 0, adjoint = 5 o 4 o 3. */
+int aahrt_apply_stage(aahrt_plan *plan, int stage, const void *in, void *out,
+                      void *stream);
+
+/* Options of the sparse solve; zero-initialised = defaults. */
+typedef struct {
+    int ista;            /* 0 (default): FISTA momentum; 1: plain ISTA (eq. ISTA) */
+    int warm_start;      /* 1: m holds the starting model on entry; else m0 = 0 */
+    int power_iters;     /* power iterations for gamma when gamma <= 0; 0 = 30 */
+    int use_graph;       /* 1: capture the iterations in a CUDA graph; 0 = eager */
+    double gamma;        /* step length; <= 0: 0.95 / (power estimate of ||L||^2) */
+    double lambda_rel;   /* > 0: lambda = lambda_rel * max|L^T d| (lambda ignored) */
+} aahrt_solve_opts;
+
+typedef struct {
+    int iters;           /* iterations run */
+    double gamma;        /* step length used */
+    double lambda;       /* lambda used */
+    double resid_norm;   /* ||d - L m||_2 of the result, FP64 accumulation */
+    double l1_norm;      /* ||m||_1 of the result */
+    double objective;    /* 1/2 resid_norm^2 + lambda * l1_norm */
+} aahrt_solve_info;
+
+/* Sparse Radon transform (eq. cost1): iters iterations of
+ *   m <- soft(z + gamma L^T (d - L z), gamma*lambda)   (eqs. ISTA, soft)
+ * with z = m (ISTA) or the FISTA extrapolation of m.  d: data_len floats;
+ * m: model_len floats, in/out.  opts and info may be NULL.  When info is
+ * non-NULL, or gamma/lambda must be estimated, the call synchronises the
+ * stream.  For batched and multi-gather plans one gamma and one lambda serve
+ * every cube. */
+int aahrt_sparse_solve(aahrt_plan *plan, const float *d, float lambda,
+                       int iters, float *m, const aahrt_solve_opts *opts,
+                       aahrt_solve_info *info, void *stream);
+
+/* Uniform curvature axis for a slowness range: q0 = pmin^2 and
+ * dq = (pmax^2 - pmin^2)/(nq - 1) (curvature is squared slowness, Sec. 2). */
+int aahrt_q_from_slowness(double pmin, double pmax, int nq, double *q0,
+                          double *dq);
+
+/* Per-stage device time.  While profiling is on, every stage launch of the
+ * plan is bracketed by CUDA events on its stream and, at
+ * aahrt_plan_stage_times (which synchronises on those events), the elapsed
+ * milliseconds are summed per stage:
+ *   0 stretch+FFT (model side)   1 Fourier slice forward
+ *   2 inverse FFT+unstretch      3 unstretch^T+FFT (data side)
+ *   4 Fourier slice adjoint      5 inverse FFT+stretch^T
+ *   6 solver updates and norms
+ * times_ms[7] and launches[7] receive the totals since profiling was
+ * turned on (either may be NULL).  Turning profiling on clears them. */
+#define AAHRT_NSTAGES 7
+int aahrt_plan_set_profiling(aahrt_plan *plan, int on);
+int aahrt_plan_stage_times(aahrt_plan *plan, double *times_ms,
+                           long long *launches);
+
+const char *aahrt_status_string(int status);
+const char *aahrt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AAHRT_H */

@@ -1,0 +1,152 @@
+// Internal structures of libaahrt: plan, device tables and stage launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "aahrt.h"
+
+namespace aahrt {
+
+constexpr int kThreadsTime = 256;
+constexpr int kThreadsSlice = 256;
+constexpr int kMinW = 4;
+constexpr int kMaxW = 12;
+
+// One trace, in azimuth-sorted order within its cube (32 bytes).
+//   A: phase per frequency bin, 0.64 fixed point of frac((q0 + cq*dq) r^2 / (Nfft ds))
+//   B: q-grid position per bin, 0.64 fixed point of frac(dq r^2 / (Nfft ds))
+// so that bin k has phase frac(k*A) and position frac(k*B) (exact modular
+// integer products; no floating-point range reduction on the device).
+struct TraceGeo {
+    unsigned long long A;
+    unsigned long long B;
+    float w0, w1;     // weights of slices j0 and (j0 + 1) mod ntheta
+    int j0;           // first azimuth slice
+    int col;          // trace index within its cube = data column
+};
+static_assert(sizeof(TraceGeo) == 32, "TraceGeo must be 32 bytes");
+
+// Work unit of the slice kernels: one cube and one group of azimuth slices
+// (all bins of the unit are separate work items).
+struct SliceGroup {
+    long long geo_off;  // first TraceGeo of the cube
+    long long x_off;    // complex offset of the cube's X[k][q][theta] block
+    long long y_off;    // complex offset of the cube's Y[k][trace] block
+    int ntr;            // traces of the cube (Y row length)
+    int ja, nj;         // owned slices [ja, ja + nj)
+    int f0, f1;         // traces with j0 in the owned slices
+    int e0, e1;         // traces with j0 == ja - 1 (mod ntheta), adjoint only
+};
+
+// Column group of the time-axis kernels (at most 2*pairs columns).
+struct ColGroup {
+    long long real_off;  // float offset of the group's first column in the
+                         // real (time-domain) array, row 0
+    long long spec_off;  // complex offset of its first column in the spectrum
+    int ld_real, ld_spec;  // row strides (elements)
+    int ncol;
+    int pad_;
+};
+
+struct DevCSR {
+    const int *rowptr;
+    const int *col;
+    const float *val;
+    int nrows;
+};
+
+enum C2REpilogue { EPI_STORE = 0, EPI_RESIDUAL = 1, EPI_FISTA = 2 };
+
+struct FistaArgs {
+    float *m;        // current iterate (in/out)
+    float *z;        // extrapolated point (in/out)
+    float gamma;
+    float thresh;    // gamma * lambda
+    float beta;      // momentum weight (t_k - 1)/t_{k+1}
+};
+
+struct Plan {
+    int device = 0;
+    // axes
+    int nt = 0, ntau = 0, nq = 0, ntheta = 0;
+    double dt = 0, q0 = 0, dq = 0;
+    int interp = AAHRT_INTERP_KEYS;
+    int w = 7;
+    double sigma_t = 2.0, fmax = 0.0;
+    int ncube = 1;          // cubes (independent geometries or gathers)
+    int ngather = 1;        // gathers per distinct geometry
+    std::vector<int> ntr;   // traces per cube
+    std::vector<long long> data_off;   // float offset of cube c in d
+    long long ntr_total = 0;
+    // stretched-time plan
+    double tmax = 0, rho = 0, ds = 0;
+    int nfft = 0, L = 0, ns = 0, kmax = 0, nbins = 0;
+    int pairs = 1;          // column pairs per time-kernel block
+    // q spreading
+    int nos = 0, Lq = 0, cq = 0;
+    double beta = 0;
+    int tgroup = 0, ngroup = 1;   // slices per group, groups per cube
+    long long model_len = 0, data_len = 0, cols_model = 0;
+    // device tables
+    float2 *tw_t = nullptr, *tw_q = nullptr;
+    float *dec = nullptr;
+    TraceGeo *geo = nullptr;
+    SliceGroup *groups = nullptr;
+    int ngroups_total = 0;
+    long long slice_items = 0;
+    int *counters = nullptr;       // work counters of the persistent kernels
+    ColGroup *cg_model = nullptr, *cg_data = nullptr;
+    int ncg_model = 0, ncg_data = 0;
+    int *csr_i = nullptr;          // all CSR index arrays (one allocation)
+    float *csr_v = nullptr;
+    DevCSR S{}, ST{}, U{}, UT{};
+    int slice_grid_fwd = 0, slice_grid_adj = 0;
+    size_t smem_r2c = 0, smem_c2r = 0, smem_sfwd = 0, smem_sadj = 0;
+    // workspace
+    float2 *X = nullptr, *Y = nullptr;
+    long long x_len = 0, y_len = 0;
+    // solver workspace (allocated on first solve)
+    float *z = nullptr, *r = nullptr, *v = nullptr;
+    double *scal = nullptr;        // device scalars of the solver
+    float *stage_m = nullptr, *stage_d = nullptr;   // staging of host buffers
+    // cached graph of the last solve
+    cudaGraphExec_t gexec = nullptr;
+    std::string gkey;
+    long long glaunches = 0;
+    // accounting
+    long long launches[AAHRT_NSTAGES] = {0};
+    bool profiling = false;
+    double prof_ms[AAHRT_NSTAGES] = {0};
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<int> ev_stage;     // stage of pending pair i (events 2i, 2i+1)
+    size_t ev_used = 0;
+    long long bytes = 0;
+};
+
+// error state
+int set_error(int code, const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what);
+
+// stage launchers (stream-ordered, no synchronisation)
+cudaError_t launch_r2c(Plan &p, bool model_side, const float *in, float2 *out,
+                       cudaStream_t st);
+cudaError_t launch_c2r(Plan &p, bool model_side, const float2 *in, float *out,
+                       int epi, const float *aux, FistaArgs fa, cudaStream_t st);
+cudaError_t launch_slice(Plan &p, bool adjoint, const float2 *in, float2 *out,
+                         cudaStream_t st);
+
+// profiling brackets around a stage launch
+void prof_begin(Plan &p, int stage, cudaStream_t st);
+void prof_end(Plan &p, cudaStream_t st);
+
+// operator application used by the C ABI and the solver
+int apply_forward(Plan &p, const float *m, float *d, cudaStream_t st,
+                  int epi = EPI_STORE, const float *dobs = nullptr);
+int apply_adjoint(Plan &p, const float *d, float *m, cudaStream_t st,
+                  int epi = EPI_STORE, FistaArgs fa = FistaArgs{});
+
+}  // namespace aahrt

@@ -1,0 +1,155 @@
+"""Convenience wrapper over the C ABI: owns a plan handle, checks tensor
+shapes/devices, and passes torch's device pointers and current CUDA stream
+to libaahrt.  PyTorch supplies device memory and streams only."""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _geom(nt, dt, ntau, nq, q0, dq, ntheta, hx, hy, keep):
+    hx = np.ascontiguousarray(hx, dtype=np.float64)
+    hy = np.ascontiguousarray(hy, dtype=np.float64)
+    if hx.shape != hy.shape or hx.ndim != 1:
+        raise ValueError("hx and hy must be 1-D arrays of equal length")
+    keep.extend([hx, hy])
+    dp = ctypes.POINTER(ctypes.c_double)
+    return L.aahrt_geom(int(nt), float(dt), int(ntau), int(nq), float(q0), float(dq),
+                        int(ntheta), int(hx.shape[0]), hx.ctypes.data_as(dp),
+                        hy.ctypes.data_as(dp))
+
+
+def _opts(interp="keys", spread_width=0, theta_group=0, ngather=1, sigma_t=0.0, fmax=0.0):
+    kind = {"keys": L.AAHRT_INTERP_KEYS, "linear": L.AAHRT_INTERP_LINEAR}[interp]
+    return L.aahrt_opts(kind, int(spread_width), int(theta_group), int(ngather),
+                        float(sigma_t), float(fmax))
+
+
+class AahrtPlan:
+    """Plan of the AAHRT operator pair on the current CUDA device."""
+
+    def __init__(self, nt, dt, ntau, nq, q0, dq, ntheta, hx, hy, *, interp="keys",
+                 spread_width=0, theta_group=0, ngather=1, sigma_t=0.0, fmax=0.0,
+                 _handle=None, _shapes=None):
+        if _handle is not None:
+            self.handle = _handle
+        else:
+            keep = []
+            g = _geom(nt, dt, ntau, nq, q0, dq, ntheta, hx, hy, keep)
+            self.handle = L.aahrt_plan_create(
+                g, _opts(interp, spread_width, theta_group, ngather, sigma_t, fmax))
+        self.info = L.aahrt_plan_query(self.handle)
+        self.nt, self.ntau, self.nq, self.ntheta = nt, ntau, nq, ntheta
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    @classmethod
+    def from_gather(cls, g, **kw):
+        return cls(**g.geom_kwargs(), **kw)
+
+    @classmethod
+    def batched(cls, gathers: Sequence, interp="keys", spread_width=0, theta_group=0,
+                sigma_t=0.0, fmax=0.0):
+        keep = []
+        geoms = [_geom(g.nt, g.dt, g.ntau, g.nq, g.q0, g.dq, g.ntheta, g.hx, g.hy, keep)
+                 for g in gathers]
+        h = L.aahrt_plan_create_batched(
+            geoms, _opts(interp, spread_width, theta_group, 1, sigma_t, fmax))
+        g0 = gathers[0]
+        return cls(g0.nt, g0.dt, g0.ntau, g0.nq, g0.q0, g0.dq, g0.ntheta, None, None,
+                   _handle=h)
+
+    # ------------------------------------------------------------------
+    @property
+    def model_len(self) -> int:
+        return int(self.info.model_len)
+
+    @property
+    def data_len(self) -> int:
+        return int(self.info.data_len)
+
+    def _check(self, t: torch.Tensor, n: int, name: str):
+        if not isinstance(t, torch.Tensor) or t.device.type != "cuda":
+            raise TypeError(f"{name} must be a CUDA tensor")
+        if t.dtype != torch.float32 or not t.is_contiguous():
+            raise TypeError(f"{name} must be contiguous float32")
+        if t.numel() != n:
+            raise ValueError(f"{name} has {t.numel()} elements, the plan needs {n}")
+
+    def forward(self, m: torch.Tensor, d: Optional[torch.Tensor] = None, stream=None):
+        """d = L m (Algorithm 1)."""
+        self._check(m, self.model_len, "m")
+        if d is None:
+            d = torch.empty(self.data_len, device=m.device, dtype=torch.float32)
+        self._check(d, self.data_len, "d")
+        L.aahrt_forward(self.handle, m.data_ptr(), d.data_ptr(), _stream_ptr(stream))
+        return d
+
+    def adjoint(self, d: torch.Tensor, m: Optional[torch.Tensor] = None, stream=None):
+        """m = L^T d (exact transpose)."""
+        self._check(d, self.data_len, "d")
+        if m is None:
+            m = torch.empty(self.model_len, device=d.device, dtype=torch.float32)
+        self._check(m, self.model_len, "m")
+        L.aahrt_adjoint(self.handle, d.data_ptr(), m.data_ptr(), _stream_ptr(stream))
+        return m
+
+    def sparse_solve(self, d: torch.Tensor, lam: float, iters: int,
+                     m: Optional[torch.Tensor] = None, *, ista=False, gamma=0.0,
+                     lambda_rel=0.0, power_iters=0, warm_start=False, use_graph=True,
+                     want_info=True, stream=None):
+        """Sparse transform (eq. cost1) by ISTA/FISTA iterations (eq. ISTA)."""
+        self._check(d, self.data_len, "d")
+        if m is None:
+            m = torch.zeros(self.model_len, device=d.device, dtype=torch.float32)
+        self._check(m, self.model_len, "m")
+        o = L.aahrt_solve_opts(int(bool(ista)), int(bool(warm_start)), int(power_iters),
+                               int(bool(use_graph)), float(gamma), float(lambda_rel))
+        info = L.aahrt_sparse_solve(self.handle, d.data_ptr(), float(lam), int(iters),
+                                    m.data_ptr(), o, want_info, _stream_ptr(stream))
+        return m, info
+
+    def apply_stage(self, stage: int, x: torch.Tensor, out: Optional[torch.Tensor] = None,
+                    stream=None):
+        """One operator stage (see aahrt_apply_stage); spectra are complex64."""
+        xs, ys = int(self.info.xspec_len), int(self.info.yspec_len)
+        n_in = [self.model_len, xs, ys, self.data_len, ys, xs][stage]
+        n_out = [xs, ys, self.data_len, ys, xs, self.model_len][stage]
+        cplx_in = stage in (1, 2, 4, 5)
+        cplx_out = stage in (0, 1, 3, 4)
+        want_in = torch.complex64 if cplx_in else torch.float32
+        if x.dtype != want_in or x.numel() != n_in or not x.is_cuda or not x.is_contiguous():
+            raise ValueError(f"stage {stage} needs a contiguous CUDA {want_in} input of {n_in}")
+        if out is None:
+            out = torch.empty(n_out, device=x.device,
+                              dtype=torch.complex64 if cplx_out else torch.float32)
+        L.aahrt_apply_stage(self.handle, stage, x.data_ptr(), out.data_ptr(),
+                            _stream_ptr(stream))
+        return out
+
+    def set_profiling(self, on: bool):
+        L.aahrt_plan_set_profiling(self.handle, on)
+
+    def stage_times(self):
+        return L.aahrt_plan_stage_times(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            L.aahrt_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

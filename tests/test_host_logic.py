@@ -1,0 +1,65 @@
+"""CPU tests of host-side logic: the shared-memory FFT groups and the
+per-trace slice arithmetic compiled for the host from the same headers the
+CUDA kernels use."""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CUDA_INC = "/usr/local/cuda/include"
+
+
+def _compile(src, out):
+    cxx = shutil.which("g++")
+    if cxx is None or not os.path.isdir(CUDA_INC):
+        pytest.skip("g++ or CUDA headers not available")
+    subprocess.run([cxx, "-O2", "-std=c++17", "-I" + CUDA_INC, src, "-o", out],
+                   check=True, capture_output=True)
+
+
+def test_fft_groups_match_dft(tmp_path):
+    exe = str(tmp_path / "fft_harness")
+    _compile(os.path.join(HERE, "host", "fft_harness.cpp"), exe)
+    r = subprocess.run([exe], capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
+    worst = float(r.stdout.strip().splitlines()[-1].split()[-1])
+    assert worst < 1e-6
+
+
+def test_trace_taps_exact(tmp_path):
+    exe = str(tmp_path / "slice_harness")
+    _compile(os.path.join(HERE, "host", "slice_math_harness.cpp"), exe)
+    rng = np.random.default_rng(0)
+    cases = []
+    for _ in range(400):
+        A = int(rng.integers(0, 2**63)) * 2 + int(rng.integers(0, 2))
+        B = int(rng.integers(0, 2**63)) * 2 + int(rng.integers(0, 2))
+        k = int(rng.integers(0, 8192))
+        Lq = int(rng.integers(4, 10))
+        W = int(rng.integers(4, 9))
+        cases.append((A, B, k, Lq, W))
+    inp = "\n".join("%d %d %d %d %d" % c for c in cases) + "\n"
+    r = subprocess.run([exe], input=inp, capture_output=True, text=True, check=True)
+    for (A, B, k, Lq, W), line in zip(cases, r.stdout.strip().splitlines()):
+        vals = line.split()
+        u0, z0, ph = int(vals[0]), float(vals[1]), float(vals[2])
+        phi = np.array([float(v) for v in vals[3:]])
+        # exact: phase = frac(k*A/2^64) in [-1/2, 1/2); position y = nos*frac(k*B/2^64)
+        pa = (k * A) % 2**64
+        ph_exact = (pa >> 32) / 2**32
+        if ph_exact >= 0.5:
+            ph_exact -= 1.0
+        assert abs(ph - ph_exact) < 2e-7
+        y = ((k * B) % 2**64 >> 32) / 2**32 * 2**Lq
+        # all taps within half a kernel width of y, first tap is floor(y - W/2) + 1
+        assert u0 == int(np.floor(y - W / 2)) + 1 or abs(y - W / 2 - round(y - W / 2)) < 1e-5
+        assert abs((y - u0) - z0) < 1e-5 * 2**Lq * 2**-20 + 2e-6
+        z = z0 - np.arange(W)
+        assert np.all(np.abs(z) <= W / 2 + 1e-5)
+        t = 2 * z / W
+        want = np.exp(2.3 * W * (np.sqrt(np.clip(1 - t * t, 0, None)) - 1))
+        np.testing.assert_allclose(phi, want, rtol=2e-5, atol=2e-6)  # edge taps are ill-conditioned in float
