@@ -12,20 +12,36 @@
 //         (a, c) -> (a + c W_{2h}^o, a - c W_{2h}^o).
 //
 // W_n = exp(-2 pi i / n) for the forward transform and its conjugate for the
-// inverse.  DIT with conjugated twiddles is the exact conjugate transpose of
-// DIF (stages reversed, each butterfly transposed), so a forward DIF and an
-// inverse DIT built from one twiddle table are adjoint to rounding.
+// inverse.  Inside a group the fused stages factor into a constant radix-2^A
+// network and one layer of twiddles (post-twiddles for DIF, pre-twiddles for
+// DIT) built from four exact table values.  DIT with conjugated twiddles is
+// the exact conjugate transpose of DIF (stages reversed, each butterfly
+// transposed), so a forward DIF and an inverse DIT from one table are
+// adjoint to rounding.  The table holds exp(-2 pi i m / N) for m < N.
 //
-// Shared-memory element i of a sequence lives at index i + (i >> 4): one pad
-// slot per 16 elements keeps the small-stride steps free of bank conflicts.
+// Shared-memory element i of a sequence lives at index
+// padi(i) = i + (i >> 4) + (i >> 8): the two pad terms keep every access
+// pattern of the kernels (unit, 16- and 256-element strides, and the
+// bit-reversed order of consecutive bins) free of bank conflicts.
+// Sequences of a batch sit ld elements apart, ld = 1 modulo the bank count.
 #pragma once
 
 #include <cuda_runtime.h>
 
 namespace aahrt {
 
-__host__ __device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
-__host__ __device__ __forceinline__ int padded_len(int n) { return n + (n >> 4); }
+__host__ __device__ __forceinline__ int padi(int i) { return i + (i >> 4) + (i >> 8); }
+__host__ __device__ __forceinline__ int padded_len(int n) { return n > 0 ? padi(n - 1) + 1 : 0; }
+// sequence stride of an interleaved (float2) batch: = 1 mod 16 float2
+__host__ __device__ __forceinline__ int ld_interleaved(int n) {
+    const int l = padded_len(n);
+    return l + ((17 - (l & 15)) & 15);
+}
+// sequence stride of a split (re, im float planes) batch: = 1 mod 32 floats
+__host__ __device__ __forceinline__ int ld_split(int n) {
+    const int l = padded_len(n);
+    return l + ((33 - (l & 31)) & 31);
+}
 
 __host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) {
     return make_float2(a.x + b.x, a.y + b.y);
@@ -60,11 +76,109 @@ __host__ __device__ __forceinline__ T ldg_ro(const T *p) {
 #endif
 }
 
-// One radix-2^A DIF group.  Sequence length N = 2^L, fused stages s..s+A-1,
-// group index g < N >> A.  tw[m] = exp(-2 pi i m / N), m < N/2.
-// INV = true uses conjugated twiddles (inverse transform).
+// Complex sequence stored interleaved (float2) with padded indexing.
+struct IBuf {
+    float2 *p;
+    __host__ __device__ __forceinline__ float2 ld(int i) const { return p[padi(i)]; }
+    __host__ __device__ __forceinline__ void st(int i, float2 v) const { p[padi(i)] = v; }
+};
+// Complex sequence stored as separate real and imaginary planes.
+struct SBuf {
+    float *re, *im;
+    __host__ __device__ __forceinline__ float2 ld(int i) const {
+        const int j = padi(i);
+        return make_float2(re[j], im[j]);
+    }
+    __host__ __device__ __forceinline__ void st(int i, float2 v) const {
+        const int j = padi(i);
+        re[j] = v.x;
+        im[j] = v.y;
+    }
+};
+// Batches: sequence b of the batch.
+struct IBatch {
+    float2 *base;
+    int ld;
+    __host__ __device__ __forceinline__ IBuf operator()(int b) const { return IBuf{base + (size_t)b * ld}; }
+};
+struct SBatch {
+    float *re, *im;
+    int ld;
+    __host__ __device__ __forceinline__ SBuf operator()(int b) const {
+        return SBuf{re + (size_t)b * ld, im + (size_t)b * ld};
+    }
+};
+
+// Constant twiddle kappa_{T,r} = exp(-+ 2 pi i r / 2^(T+1)), r < 2^T, of the
+// radix-2 stages inside a group (compile-time after unrolling).
+template <bool INV>
+__host__ __device__ __forceinline__ float2 kappa_mul(float2 c, int T, int r) {
+    if (r == 0) return c;
+    if (T == 1 || (T == 2 && r == 2) || (T == 3 && r == 4)) {      // -i (+i inverse)
+        return INV ? make_float2(-c.y, c.x) : make_float2(c.y, -c.x);
+    }
+    const float h = 0.70710678118654752440f;
+    if ((T == 2 && r == 1) || (T == 3 && r == 2)) {                  // exp(-+ i pi/4)
+        return INV ? make_float2(h * (c.x - c.y), h * (c.x + c.y))
+                   : make_float2(h * (c.x + c.y), h * (c.y - c.x));
+    }
+    if ((T == 2 && r == 3) || (T == 3 && r == 6)) {                  // exp(-+ 3 i pi/4)
+        return INV ? make_float2(-h * (c.x + c.y), h * (c.x - c.y))
+                   : make_float2(h * (c.y - c.x), -h * (c.x + c.y));
+    }
+    // T == 3, r odd: exp(-+ i pi r / 8)
+    const float c8 = 0.92387953251128675613f, s8 = 0.38268343236508977173f;
+    float wr, wi;
+    switch (r) {
+        case 1: wr = c8; wi = s8; break;
+        case 3: wr = s8; wi = c8; break;
+        case 5: wr = -s8; wi = c8; break;
+        default: wr = -c8; wi = s8; break;   // r == 7
+    }
+    if (!INV) wi = -wi;
+    return make_float2(c.x * wr - c.y * wi, c.x * wi + c.y * wr);
+}
+
+// w[r] = exp(-+ 2 pi i q r / 2^X) for r < 2^A from four exact table values
+// (r = 1, 2, 4, 8) and products; tw holds exp(-2 pi i m / N), m < N, N = 2^L.
 template <int A, bool INV>
-__host__ __device__ __forceinline__ void dif_group(float2 *p, int L, int s, int g,
+__host__ __device__ __forceinline__ void group_twiddles(int q, int L, int X,
+                                                        const float2 *__restrict__ tw,
+                                                        float2 *w) {
+    constexpr int R = 1 << A;
+    const int N = 1 << L;
+    const int sh = L - X;
+    w[0] = make_float2(1.f, 0.f);
+#pragma unroll
+    for (int b = 0; b < A; ++b) {
+        float2 t = ldg_ro(tw + ((((long long)q << b) << sh) & (N - 1)));
+        if (INV) t.y = -t.y;
+        w[1 << b] = t;
+    }
+#pragma unroll
+    for (int r = 3; r < R; ++r) {
+        if ((r & (r - 1)) == 0) continue;
+        int hi = r;
+        while (hi & (hi - 1)) hi &= hi - 1;      // highest set bit
+        w[r] = cmul(w[hi], w[r - hi]);
+    }
+}
+
+template <int A>
+__host__ __device__ __forceinline__ int rev_bits_c(int m) {
+    int r = 0;
+#pragma unroll
+    for (int i = 0; i < A; ++i) r |= ((m >> i) & 1) << (A - 1 - i);
+    return r;
+}
+
+// One radix-2^A DIF group: fused stages s..s+A-1 of the DIF recursion for a
+// sequence of N = 2^L, group index g < N >> A.  Written as the constant
+// radix-2^A DIF network followed by the post-twiddles
+// exp(-2 pi i j rev_A(m) / 2^(lhs+A)) of output m (j = offset of the group).
+// INV = true conjugates every twiddle (inverse transform).
+template <int A, bool INV, class B>
+__host__ __device__ __forceinline__ void dif_group(const B &p, int L, int s, int g,
                                                    const float2 *__restrict__ tw) {
     constexpr int R = 1 << A;
     const int lhs = L - s - A;                 // log2 of the smallest half span
@@ -72,58 +186,61 @@ __host__ __device__ __forceinline__ void dif_group(float2 *p, int L, int s, int 
     const int base = ((g >> lhs) << (L - s)) | j;
     float2 v[R];
 #pragma unroll
-    for (int m = 0; m < R; ++m) v[m] = p[padi(base + (m << lhs))];
+    for (int m = 0; m < R; ++m) v[m] = p.ld(base + (m << lhs));
 #pragma unroll
     for (int t = 0; t < A; ++t) {
         const int Mt = R >> (t + 1);
+        const int T = A - 1 - t;               // log2 Mt
 #pragma unroll
         for (int m = 0; m < R; ++m) {
             if (m & Mt) continue;
-            const int o = j + ((m & (Mt - 1)) << lhs);
             const float2 a = v[m], c = v[m + Mt];
             v[m] = cadd(a, c);
-            const float2 d = csub(a, c);
-            if (o == 0) {
-                v[m + Mt] = d;
-            } else {
-                const float2 w = ldg_ro(tw + (o << (s + t)));
-                v[m + Mt] = INV ? cmulc(d, w) : cmul(d, w);
-            }
+            v[m + Mt] = kappa_mul<INV>(csub(a, c), T, m & (Mt - 1));
         }
     }
+    if (j != 0) {
+        float2 w[R];
+        group_twiddles<A, INV>(j, L, lhs + A, tw, w);
 #pragma unroll
-    for (int m = 0; m < R; ++m) p[padi(base + (m << lhs))] = v[m];
+        for (int m = 1; m < R; ++m) v[m] = cmul(v[m], w[rev_bits_c<A>(m)]);
+    }
+#pragma unroll
+    for (int m = 0; m < R; ++m) p.st(base + (m << lhs), v[m]);
 }
 
-// One radix-2^A DIT group (fused stages s..s+A-1 of the DIT recursion).
-template <int A, bool INV>
-__host__ __device__ __forceinline__ void dit_group(float2 *p, int L, int s, int g,
+// One radix-2^A DIT group (fused stages s..s+A-1 of the DIT recursion):
+// pre-twiddles exp(-2 pi i low rev_A(m) / 2^(s+A)) on input m, then the
+// constant radix-2^A DIT network.
+template <int A, bool INV, class B>
+__host__ __device__ __forceinline__ void dit_group(const B &p, int L, int s, int g,
                                                    const float2 *__restrict__ tw) {
     constexpr int R = 1 << A;
     const int low = g & ((1 << s) - 1);
     const int base = ((g >> s) << (s + A)) | low;
     float2 v[R];
 #pragma unroll
-    for (int m = 0; m < R; ++m) v[m] = p[padi(base + (m << s))];
+    for (int m = 0; m < R; ++m) v[m] = p.ld(base + (m << s));
+    if (low != 0) {
+        float2 w[R];
+        group_twiddles<A, INV>(low, L, s + A, tw, w);
+#pragma unroll
+        for (int m = 1; m < R; ++m) v[m] = cmul(v[m], w[rev_bits_c<A>(m)]);
+    }
 #pragma unroll
     for (int t = 0; t < A; ++t) {
         const int Mt = 1 << t;
 #pragma unroll
         for (int m = 0; m < R; ++m) {
             if (m & Mt) continue;
-            const int o = low + ((m & (Mt - 1)) << s);
-            float2 c = v[m + Mt];
-            if (o != 0) {
-                const float2 w = ldg_ro(tw + (o << (L - 1 - (s + t))));
-                c = INV ? cmulc(c, w) : cmul(c, w);
-            }
+            const float2 c = kappa_mul<INV>(v[m + Mt], t, m & (Mt - 1));
             const float2 a = v[m];
             v[m] = cadd(a, c);
             v[m + Mt] = csub(a, c);
         }
     }
 #pragma unroll
-    for (int m = 0; m < R; ++m) p[padi(base + (m << s))] = v[m];
+    for (int m = 0; m < R; ++m) p.st(base + (m << s), v[m]);
 }
 
 // Fused-step schedule: steps of 4 radix-2 stages, the remainder last.
@@ -132,78 +249,51 @@ __host__ __device__ __forceinline__ int fused_width(int L, int s) {
     return r >= 4 ? 4 : r;
 }
 
-#ifdef __CUDACC__
-// nb sequences of length 2^L at buf + b*ld (ld in float2, padded layout
-// inside each sequence).  Must be called by every thread of the block; ends
-// with a __syncthreads.
-template <bool INV>
-__device__ void block_fft_dif(float2 *buf, int ld, int nb, int L,
-                              const float2 *__restrict__ tw) {
-    for (int s = 0; s < L;) {
-        const int A = fused_width(L, s);
-        const int ng = 1 << (L - A);
-        const int total = ng * nb;
-        for (int w = threadIdx.x; w < total; w += blockDim.x) {
-            float2 *p = buf + (size_t)(w >> (L - A)) * ld;
-            const int g = w & (ng - 1);
-            switch (A) {
-                case 4: dif_group<4, INV>(p, L, s, g, tw); break;
-                case 3: dif_group<3, INV>(p, L, s, g, tw); break;
-                case 2: dif_group<2, INV>(p, L, s, g, tw); break;
-                default: dif_group<1, INV>(p, L, s, g, tw); break;
-            }
+template <bool DIF, bool INV, class Batch>
+__host__ __device__ __forceinline__ void fft_group(const Batch &bt, int L, int s, int A, int w,
+                                                   const float2 *__restrict__ tw) {
+    const auto p = bt(w >> (L - A));
+    const int g = w & ((1 << (L - A)) - 1);
+    if (DIF) {
+        switch (A) {
+            case 4: dif_group<4, INV>(p, L, s, g, tw); break;
+            case 3: dif_group<3, INV>(p, L, s, g, tw); break;
+            case 2: dif_group<2, INV>(p, L, s, g, tw); break;
+            default: dif_group<1, INV>(p, L, s, g, tw); break;
         }
-        s += A;
-        __syncthreads();
+    } else {
+        switch (A) {
+            case 4: dit_group<4, INV>(p, L, s, g, tw); break;
+            case 3: dit_group<3, INV>(p, L, s, g, tw); break;
+            case 2: dit_group<2, INV>(p, L, s, g, tw); break;
+            default: dit_group<1, INV>(p, L, s, g, tw); break;
+        }
     }
 }
 
-template <bool INV>
-__device__ void block_fft_dit(float2 *buf, int ld, int nb, int L,
-                              const float2 *__restrict__ tw) {
+#ifdef __CUDACC__
+// nb sequences of length 2^L (bt(b) gives sequence b).  Must be called by
+// every thread of the block; ends with a __syncthreads.
+template <bool DIF, bool INV, class Batch>
+__device__ void block_fft(const Batch &bt, int nb, int L, const float2 *__restrict__ tw) {
     for (int s = 0; s < L;) {
         const int A = fused_width(L, s);
-        const int ng = 1 << (L - A);
-        const int total = ng * nb;
-        for (int w = threadIdx.x; w < total; w += blockDim.x) {
-            float2 *p = buf + (size_t)(w >> (L - A)) * ld;
-            const int g = w & (ng - 1);
-            switch (A) {
-                case 4: dit_group<4, INV>(p, L, s, g, tw); break;
-                case 3: dit_group<3, INV>(p, L, s, g, tw); break;
-                case 2: dit_group<2, INV>(p, L, s, g, tw); break;
-                default: dit_group<1, INV>(p, L, s, g, tw); break;
-            }
-        }
+        const int total = nb << (L - A);
+        for (int w = threadIdx.x; w < total; w += blockDim.x)
+            fft_group<DIF, INV>(bt, L, s, A, w, tw);
         s += A;
         __syncthreads();
     }
 }
 #endif
 
-// Host reference driver of the same groups (used by the CPU test harness).
-template <bool DIF, bool INV>
-inline void host_fft(float2 *p, int L, const float2 *tw) {
+// Host driver of the same groups (used by the CPU test harness).
+template <bool DIF, bool INV, class Batch>
+inline void host_fft(const Batch &bt, int nb, int L, const float2 *tw) {
     for (int s = 0; s < L;) {
         const int A = fused_width(L, s);
-        const int ng = 1 << (L - A);
-        for (int g = 0; g < ng; ++g) {
-            if (DIF) {
-                switch (A) {
-                    case 4: dif_group<4, INV>(p, L, s, g, tw); break;
-                    case 3: dif_group<3, INV>(p, L, s, g, tw); break;
-                    case 2: dif_group<2, INV>(p, L, s, g, tw); break;
-                    default: dif_group<1, INV>(p, L, s, g, tw); break;
-                }
-            } else {
-                switch (A) {
-                    case 4: dit_group<4, INV>(p, L, s, g, tw); break;
-                    case 3: dit_group<3, INV>(p, L, s, g, tw); break;
-                    case 2: dit_group<2, INV>(p, L, s, g, tw); break;
-                    default: dit_group<1, INV>(p, L, s, g, tw); break;
-                }
-            }
-        }
+        const int total = nb << (L - A);
+        for (int w = 0; w < total; ++w) fft_group<DIF, INV>(bt, L, s, A, w, tw);
         s += A;
     }
 }

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "aahrt.h"
+#include "slice_math.cuh"
 
 namespace aahrt {
 
@@ -15,6 +16,7 @@ constexpr int kThreadsTime = 256;
 constexpr int kThreadsSlice = 256;
 constexpr int kMinW = 4;
 constexpr int kMaxW = 12;
+constexpr int kMaxGroupSlices = 256;   // azimuth slices one slice-kernel block may own
 
 // One trace, in azimuth-sorted order within its cube (32 bytes).
 //   A: phase per frequency bin, 0.64 fixed point of frac((q0 + cq*dq) r^2 / (Nfft ds))
@@ -40,6 +42,7 @@ struct SliceGroup {
     int ja, nj;         // owned slices [ja, ja + nj)
     int f0, f1;         // traces with j0 in the owned slices
     int e0, e1;         // traces with j0 == ja - 1 (mod ntheta), adjoint only
+    long long ss_off;   // offset of the cube's slice-start table (ntheta + 1 ints)
 };
 
 // Column group of the time-axis kernels (at most 2*pairs columns).
@@ -52,11 +55,22 @@ struct ColGroup {
     int pad_;
 };
 
-struct DevCSR {
-    const int *rowptr;
-    const int *col;
-    const float *val;
-    int nrows;
+// Resampler tables.  Output row o of the stretch S (or its undoing U) sits
+// at position fl + fr of the input axis; the transposed operator reads, for
+// output o, the contiguous source rows lo .. lo + cnt - 1.
+struct RowPos {
+    int fl;
+    float fr;
+};
+struct RowRange {
+    int lo;
+    int cnt;
+};
+struct DevResampler {
+    const RowPos *pos;      // per output row (S, U) or per source row (S^T, U^T)
+    const RowRange *rng;    // per output row of a transposed operator, else null
+    int nrows;              // output rows
+    int npos;               // entries of pos
 };
 
 enum C2REpilogue { EPI_STORE = 0, EPI_RESIDUAL = 1, EPI_FISTA = 2 };
@@ -96,16 +110,21 @@ struct Plan {
     float *dec = nullptr;
     TraceGeo *geo = nullptr;
     SliceGroup *groups = nullptr;
+    int *slice_start = nullptr;    // per distinct geometry: first sorted trace of each slice
     int ngroups_total = 0;
     long long slice_items = 0;
     int *counters = nullptr;       // work counters of the persistent kernels
     ColGroup *cg_model = nullptr, *cg_data = nullptr;
     int ncg_model = 0, ncg_data = 0;
-    int *csr_i = nullptr;          // all CSR index arrays (one allocation)
-    float *csr_v = nullptr;
-    DevCSR S{}, ST{}, U{}, UT{};
+    RowPos *posS = nullptr, *posU = nullptr;       // resampler tables
+    RowRange *rngST = nullptr, *rngUT = nullptr;
+    DevResampler S{}, ST{}, U{}, UT{};
+    EsPoly poly{};                 // Horner coefficients of the spreading kernel
+    double phimax = 0;             // bound on sum_i phi_i over positions
+    int lp = 0;                    // log2(pairs)
     int slice_grid_fwd = 0, slice_grid_adj = 0;
-    size_t smem_r2c = 0, smem_c2r = 0, smem_sfwd = 0, smem_sadj = 0;
+    size_t smem_r2c_model = 0, smem_r2c_data = 0, smem_c2r_model = 0, smem_c2r_data = 0;
+    size_t smem_sfwd = 0, smem_sadj = 0;
     // workspace
     float2 *X = nullptr, *Y = nullptr;
     long long x_len = 0, y_len = 0;
@@ -126,6 +145,17 @@ struct Plan {
     size_t ev_used = 0;
     long long bytes = 0;
 };
+
+// Raise a kernel's dynamic shared memory limit to what the device allows
+// beside the kernel's static shared memory.
+template <typename F>
+inline cudaError_t raise_smem_limit(F *func, int max_smem) {
+    cudaFuncAttributes at;
+    cudaError_t e = cudaFuncGetAttributes(&at, func);
+    if (e) return e;
+    return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                max_smem - (int)at.sharedSizeBytes);
+}
 
 // error state
 int set_error(int code, const char *fmt, ...);

@@ -4,6 +4,7 @@
 // "spline" interpolation; here Keys' cubic convolution or linear), the
 // spreading kernel of the q-slice, device workspace and work lists.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -16,8 +17,8 @@
 
 namespace aahrt {
 
-cudaError_t set_time_kernel_attrs(size_t smem);
-cudaError_t configure_slice_kernels(Plan &p, int num_sms);
+cudaError_t set_time_kernel_attrs(int lp, int interp, int max_smem);
+cudaError_t configure_slice_kernels(Plan &p, int num_sms, int max_smem);
 
 static thread_local char g_err[1024] = "";
 
@@ -49,66 +50,48 @@ static int ilog2(long long n) {
     return l;
 }
 
-// Keys' cubic convolution kernel, a = -1/2.
-static double keys_kernel(double x) {
-    const double a = -0.5;
-    const double ax = std::fabs(x);
-    if (ax <= 1.0) return (a + 2.0) * ax * ax * ax - (a + 3.0) * ax * ax + 1.0;
-    if (ax < 2.0) return a * ax * ax * ax - 5.0 * a * ax * ax + 8.0 * a * ax - 4.0 * a;
-    return 0.0;
-}
-static double linear_kernel(double x) {
-    const double ax = std::fabs(x);
-    return ax < 1.0 ? 1.0 - ax : 0.0;
-}
-
-struct HostCSR {
-    std::vector<int> rowptr, col;
-    std::vector<float> val;
-    int nrows = 0;
-};
-
-// Interpolation rows at fractional positions pos[o] of an input axis of n_in
-// samples; taps outside the axis (and exact zeros) are left out.
-static HostCSR resampler(const std::vector<double> &pos, int n_in, int interp) {
-    HostCSR c;
-    c.nrows = (int)pos.size();
-    c.rowptr.push_back(0);
-    const int t0 = interp == AAHRT_INTERP_KEYS ? -1 : 0;
-    const int t1 = interp == AAHRT_INTERP_KEYS ? 2 : 1;
-    for (double u : pos) {
-        const long long b = (long long)std::floor(u);
-        for (int t = t0; t <= t1; ++t) {
-            const long long i = b + t;
-            if (i < 0 || i >= n_in) continue;
-            const double wv = interp == AAHRT_INTERP_KEYS ? keys_kernel(u - (double)i)
-                                                          : linear_kernel(u - (double)i);
-            if (wv == 0.0) continue;
-            c.col.push_back((int)i);
-            c.val.push_back((float)wv);
-        }
-        c.rowptr.push_back((int)c.col.size());
+// Position of every output row of a resampler on its input axis.
+static std::vector<RowPos> row_positions(const std::vector<double> &pos) {
+    std::vector<RowPos> out(pos.size());
+    for (size_t o = 0; o < pos.size(); ++o) {
+        const double fl = std::floor(pos[o]);
+        out[o].fl = (int)fl;
+        out[o].fr = (float)(pos[o] - fl);
     }
-    return c;
+    return out;
 }
 
-// Exact transpose (same float weights) of a CSR with ncols columns.
-static HostCSR transpose(const HostCSR &a, int ncols) {
-    HostCSR t;
-    t.nrows = ncols;
-    t.rowptr.assign(ncols + 1, 0);
-    for (int c : a.col) t.rowptr[c + 1]++;
-    for (int i = 0; i < ncols; ++i) t.rowptr[i + 1] += t.rowptr[i];
-    t.col.resize(a.col.size());
-    t.val.resize(a.val.size());
-    std::vector<int> fill(t.rowptr.begin(), t.rowptr.end() - 1);
-    for (int r = 0; r < a.nrows; ++r)
-        for (int e = a.rowptr[r]; e < a.rowptr[r + 1]; ++e) {
-            const int d = fill[a.col[e]]++;
-            t.col[d] = r;
-            t.val[d] = a.val[e];
+// Source ranges of the transpose: output o of the transpose collects every
+// row r whose taps fl_r + t (t in [t0, t0 + ntap), inside [0, n_out)) include
+// o.  Since fl_r is non-decreasing, the sources are contiguous and come in
+// segments of decreasing t; the segment of tap t0 + q holds (cnt >> 8q) & 255
+// rows.  Returns false if a range is not contiguous or a segment exceeds 255.
+static bool transpose_ranges(const std::vector<RowPos> &pos, int n_out, int interp,
+                             std::vector<RowRange> *rng) {
+    const int t0 = interp == AAHRT_INTERP_KEYS ? -1 : 0;
+    const int ntap = interp == AAHRT_INTERP_KEYS ? 4 : 2;
+    std::vector<int> lo(n_out, 0), last(n_out, -2), total(n_out, 0);
+    std::vector<std::array<int, 4>> seg(n_out, std::array<int, 4>{0, 0, 0, 0});
+    for (int r = 0; r < (int)pos.size(); ++r)
+        for (int q = 0; q < ntap; ++q) {
+            const int o = pos[r].fl + t0 + q;
+            if (o < 0 || o >= n_out) continue;
+            if (total[o] == 0) lo[o] = r;
+            else if (r != last[o] + 1) return false;
+            last[o] = r;
+            total[o]++;
+            seg[o][q]++;
         }
-    return t;
+    rng->resize(n_out);
+    for (int o = 0; o < n_out; ++o) {
+        unsigned packed = 0;
+        for (int q = 0; q < ntap; ++q) {
+            if (seg[o][q] > 255) return false;
+            packed |= (unsigned)seg[o][q] << (8 * q);
+        }
+        (*rng)[o] = RowRange{lo[o], (int)packed};
+    }
+    return true;
 }
 
 // Fourier transform of the spreading kernel phi(z) = exp(beta(sqrt(1-(2z/W)^2)-1)),
@@ -196,8 +179,8 @@ void free_plan(Plan *p) {
     cudaSetDevice(p->device);
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
-    void *ptrs[] = {p->tw_t, p->tw_q, p->dec, p->geo, p->groups, p->counters,
-                    p->cg_model, p->cg_data, p->csr_i, p->csr_v, p->X, p->Y,
+    void *ptrs[] = {p->tw_t, p->tw_q, p->dec, p->geo, p->groups, p->slice_start, p->counters,
+                    p->cg_model, p->cg_data, p->posS, p->posU, p->rngST, p->rngUT, p->X, p->Y,
                     p->z, p->r, p->v, p->scal, p->stage_m, p->stage_d};
     for (void *q : ptrs)
         if (q) cudaFree(q);
@@ -283,21 +266,19 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
         free_plan(p);
         return set_error(AAHRT_ERR_INVALID_ARG, "all offsets are zero");
     }
+    int rc_fail = AAHRT_OK;
     p->tmax = (p->nt - 1) * p->dt;
     const double qabs = std::max(std::fabs(p->q0), std::fabs(p->q0 + (p->nq - 1) * p->dq));
     p->rho = qabs * r2max / (p->tmax * p->tmax);
     const double want = std::ceil(p->sigma_t * p->nt * (1.0 + p->rho));
-    if (!(want < 1e9)) {
+    if (!(want <= 16384.0)) {
+        rc_fail = set_error(AAHRT_ERR_UNSUPPORTED,
+                            "FFT frame of %.0f samples or more exceeds 16384 (nt = %d, rho = %g)",
+                            want, p->nt, p->rho);
         free_plan(p);
-        return set_error(AAHRT_ERR_UNSUPPORTED, "FFT frame too long (rho = %g)", p->rho);
+        return rc_fail;
     }
     p->nfft = (int)next_pow2((long long)want);
-    if (p->nfft > 16384) {
-        free_plan(p);
-        return set_error(AAHRT_ERR_UNSUPPORTED,
-                         "FFT frame of %d samples exceeds 16384 (nt = %d, rho = %g)", p->nfft,
-                         p->nt, p->rho);
-    }
     p->L = ilog2(p->nfft);
     p->ns = (int)std::floor((p->nfft - 2) / (1.0 + p->rho)) + 1;
     p->ds = p->tmax * p->tmax / (p->ns - 1);
@@ -306,6 +287,7 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
         p->kmax = std::min(p->kmax, (int)std::floor(p->fmax * p->nfft * p->ds));
     p->nbins = p->kmax + 1;
     p->pairs = std::max(1, std::min(8, 8192 / p->nfft));
+    p->lp = ilog2(p->pairs);
 
     // ----------------------------------------------------- q spreading
     p->nos = (int)std::max(16LL, next_pow2(2LL * p->nq));
@@ -318,8 +300,8 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
         dec[l] = (float)(1.0 / es_fourier((double)(l - p->cq) / p->nos, p->beta, W));
 
     // --------------------------------------------------- azimuth groups
-    const int ldq = padded_len(p->nos);
-    const size_t per_slice = (size_t)ldq * sizeof(float2);
+    const size_t per_slice = (size_t)std::max(ld_interleaved(p->nos), ld_split(p->nos)) *
+                             sizeof(float2);
     if (opts.theta_group > 0) {
         p->tgroup = std::min(opts.theta_group, p->ntheta);
     } else {
@@ -333,6 +315,7 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
             p->tgroup = (p->ntheta + ng - 1) / ng;
         }
     }
+    if (p->tgroup > kMaxGroupSlices) p->tgroup = kMaxGroupSlices;
     p->ngroup = (p->ntheta + p->tgroup - 1) / p->tgroup;
     if (p->ngroup == 1) p->tgroup = p->ntheta;
 
@@ -341,9 +324,11 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
     for (int c = 0; c < ndist; ++c) cg[c] = bin_cube(*p, geoms[c].hx, geoms[c].hy, geoms[c].ntr);
     std::vector<long long> geo_off(ndist, 0);
     std::vector<TraceGeo> geo_all;
+    std::vector<int> ss_all;
     for (int c = 0; c < ndist; ++c) {
         geo_off[c] = (long long)geo_all.size();
         geo_all.insert(geo_all.end(), cg[c].sorted.begin(), cg[c].sorted.end());
+        ss_all.insert(ss_all.end(), cg[c].start.begin(), cg[c].start.end());
     }
     p->ntr.resize(ncube);
     p->data_off.resize(ncube);
@@ -371,6 +356,7 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
         for (int gi = 0; gi < p->ngroup; ++gi) {
             SliceGroup s;
             s.geo_off = geo_off[dc];
+            s.ss_off = (long long)dc * (p->ntheta + 1);
             s.x_off = (long long)c * p->nbins * C;
             s.y_off = y_off[c];
             s.ntr = p->ntr[c];
@@ -426,32 +412,37 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
     std::vector<double> upos(p->ns), vpos(p->nt);
     for (int n = 0; n < p->ns; ++n) upos[n] = std::sqrt(n * p->ds) / p->dt;
     for (int i = 0; i < p->nt; ++i) vpos[i] = (i * p->dt) * (i * p->dt) / p->ds;
-    const HostCSR S = resampler(upos, p->ntau, p->interp);
-    const HostCSR ST = transpose(S, p->ntau);
-    const HostCSR U = resampler(vpos, p->ns, p->interp);
-    const HostCSR UT = transpose(U, p->ns);
-    std::vector<int> ci;
-    std::vector<float> cv;
-    size_t offs_i[4][3], offs_v[4];
-    const HostCSR *all[4] = {&S, &ST, &U, &UT};
-    for (int t = 0; t < 4; ++t) {
-        offs_i[t][0] = ci.size();
-        ci.insert(ci.end(), all[t]->rowptr.begin(), all[t]->rowptr.end());
-        offs_i[t][1] = ci.size();
-        ci.insert(ci.end(), all[t]->col.begin(), all[t]->col.end());
-        offs_v[t] = cv.size();
-        cv.insert(cv.end(), all[t]->val.begin(), all[t]->val.end());
-        cv.push_back(0.f);  // keeps every table non-empty
+    const std::vector<RowPos> posS = row_positions(upos), posU = row_positions(vpos);
+    std::vector<RowRange> rngST, rngUT;
+    if (!transpose_ranges(posS, p->ntau, p->interp, &rngST) ||
+        !transpose_ranges(posU, p->ns, p->interp, &rngUT)) {
+        rc_fail = set_error(AAHRT_ERR_UNSUPPORTED, "resampler transpose is not banded");
+        free_plan(p);
+        return rc_fail;
+    }
+    fit_es_poly(W, p->beta, &p->poly);
+    {   // bound on the summed kernel weights of one trace, with margin
+        double mx = 0.0;
+        for (int s = 0; s <= 2000; ++s) {
+            const double g = -0.5 + s / 2000.0;
+            double sum = 0.0;
+            for (int i = 0; i < W; ++i) {
+                double v = 0.0;
+                for (int d = W + 1; d >= 0; --d) v = v * g + p->poly.c[d][i];
+                sum += std::fabs(v);
+            }
+            mx = std::max(mx, sum);
+        }
+        p->phimax = 1.05 * mx;
     }
 
     // ------------------------------------------------------- twiddles
     auto twiddles = [](int N) {
-        std::vector<float2> tw(std::max(1, N / 2));
-        for (int m = 0; m < N / 2; ++m) {
+        std::vector<float2> tw(std::max(1, N));
+        for (int m = 0; m < N; ++m) {
             const double a = -2.0 * M_PI * m / N;
             tw[m] = make_float2((float)std::cos(a), (float)std::sin(a));
         }
-        if (N < 2) tw[0] = make_float2(1.f, 0.f);
         return tw;
     };
 
@@ -474,39 +465,51 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
     AAHRT_TRY(upload(&p->dec, dec), "upload deapodisation");
     AAHRT_TRY(upload(&p->geo, geo_all), "upload geometry");
     AAHRT_TRY(upload(&p->groups, groups), "upload work list");
+    AAHRT_TRY(upload(&p->slice_start, ss_all), "upload slice table");
     AAHRT_TRY(upload(&p->cg_model, cgm), "upload column groups");
     AAHRT_TRY(upload(&p->cg_data, cgd), "upload column groups");
-    AAHRT_TRY(upload(&p->csr_i, ci), "upload resamplers");
-    AAHRT_TRY(upload(&p->csr_v, cv), "upload resamplers");
+    AAHRT_TRY(upload(&p->posS, posS), "upload resamplers");
+    AAHRT_TRY(upload(&p->posU, posU), "upload resamplers");
+    AAHRT_TRY(upload(&p->rngST, rngST), "upload resamplers");
+    AAHRT_TRY(upload(&p->rngUT, rngUT), "upload resamplers");
     AAHRT_TRY(cudaMalloc((void **)&p->counters, 16 * sizeof(int)), "alloc counters");
     AAHRT_TRY(cudaMemset(p->counters, 0, 16 * sizeof(int)), "clear counters");
-    DevCSR *dst[4] = {&p->S, &p->ST, &p->U, &p->UT};
-    for (int t = 0; t < 4; ++t) {
-        dst[t]->rowptr = p->csr_i + offs_i[t][0];
-        dst[t]->col = p->csr_i + offs_i[t][1];
-        dst[t]->val = p->csr_v + offs_v[t];
-        dst[t]->nrows = all[t]->nrows;
-    }
+    p->S = DevResampler{p->posS, nullptr, p->ns, p->ns};
+    p->ST = DevResampler{p->posS, p->rngST, p->ntau, p->ns};
+    p->U = DevResampler{p->posU, nullptr, p->nt, p->nt};
+    p->UT = DevResampler{p->posU, p->rngUT, p->ns, p->nt};
     AAHRT_TRY(cudaMalloc((void **)&p->X, std::max<long long>(1, p->x_len) * sizeof(float2)),
               "alloc X workspace");
     AAHRT_TRY(cudaMalloc((void **)&p->Y, std::max<long long>(1, p->y_len) * sizeof(float2)),
               "alloc Y workspace");
 
-    p->smem_r2c = (size_t)p->pairs * padded_len(p->nfft) * sizeof(float2);
-    p->smem_c2r = p->smem_r2c;
-    p->smem_sfwd = (size_t)(p->tgroup + (p->ngroup > 1 ? 1 : 0)) * per_slice;
-    p->smem_sadj = (size_t)p->tgroup * per_slice;
+    const size_t fftb = (size_t)p->pairs * ld_interleaved(p->nfft) * sizeof(float2);
+    p->smem_r2c_model = fftb + (size_t)p->ntau * 2 * p->pairs * sizeof(float);
+    p->smem_r2c_data = fftb + (size_t)p->nt * 2 * p->pairs * sizeof(float) +
+                       (size_t)p->nt * sizeof(float);
+    p->smem_c2r_data = fftb;
+    p->smem_c2r_model = fftb + (size_t)p->ns * sizeof(float);
+    const size_t smem_r2c = std::max(p->smem_r2c_model, p->smem_r2c_data);
+    const size_t smem_c2r = std::max(p->smem_c2r_model, p->smem_c2r_data);
+    p->smem_sfwd = (size_t)(p->tgroup + (p->ngroup > 1 ? 1 : 0)) * ld_interleaved(p->nos) *
+                   sizeof(float2);
+    p->smem_sadj = (size_t)p->tgroup * ld_split(p->nos) * 2 * sizeof(float);
     int max_smem = 0;
     AAHRT_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin,
                                      p->device), "device query");
-    if ((int)p->smem_r2c > max_smem || (int)p->smem_sfwd > max_smem) {
+    if ((int)smem_r2c > max_smem || (int)smem_c2r > max_smem || (int)p->smem_sfwd > max_smem ||
+        (int)p->smem_sadj > max_smem) {
+        rc_fail = set_error(AAHRT_ERR_UNSUPPORTED,
+                            "shared memory per block (%zu / %zu bytes) exceeds %d; lower "
+                            "theta_group", smem_r2c, p->smem_sfwd, max_smem);
         free_plan(p);
-        return set_error(AAHRT_ERR_UNSUPPORTED,
-                         "shared memory per block (%zu / %zu bytes) exceeds %d; lower "
-                         "theta_group", p->smem_r2c, p->smem_sfwd, max_smem);
+        return rc_fail;
     }
-    AAHRT_TRY(set_time_kernel_attrs(p->smem_r2c), "kernel attributes");
-    AAHRT_TRY(configure_slice_kernels(*p, num_sms), "slice kernel configuration");
+    // The dynamic shared memory limit is a property of each kernel function,
+    // shared by every plan of the process: raise it to the device maximum once
+    // so no plan lowers it under another.
+    AAHRT_TRY(set_time_kernel_attrs(p->lp, p->interp, max_smem), "kernel attributes");
+    AAHRT_TRY(configure_slice_kernels(*p, num_sms, max_smem), "slice kernel configuration");
 #undef AAHRT_TRY
     *out = p;
     return AAHRT_OK;

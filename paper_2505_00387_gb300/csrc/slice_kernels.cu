@@ -6,9 +6,14 @@
 // evaluated as a type-2 non-uniform DFT along q: the slice columns are
 // deapodised, centred, DFT'd on an nos-point grid in shared memory, and each
 // trace interpolates W grid points per slice with the spreading kernel.
-// Adjoint: each trace spreads scale * conj(phase) * Y into the grid with
-// shared-memory atomics, the grid is inverse-DFT'd and deapodised: the exact
-// transpose of the forward (same taps, weights, phases and twiddles).
+// Adjoint: each trace spreads scale * conj(phase) * Y into the grid, the grid
+// is inverse-DFT'd and deapodised: the transpose of the forward (same taps,
+// weights, phases and twiddles).  The spread accumulates in 32-bit fixed
+// point with native shared-memory integer atomics (real and imaginary parts in
+// separate planes).  Each azimuth slice gets its own scale
+// 2^30 / (Phi_max * scale * sum_h w_h |y_h|) over the traces that reach it, so
+// no grid sum can exceed 2^30 and the rounding of each contribution stays at
+// the level of FP32 rounding of the slice's values.
 //
 // Work items are (cube, azimuth group, bin); a persistent grid pulls them
 // from an atomic counter (reset by the launcher), largest groups first.
@@ -21,20 +26,33 @@ namespace aahrt {
 struct SliceArgs {
     const TraceGeo *__restrict__ geo;
     const SliceGroup *__restrict__ groups;
+    const int *__restrict__ slice_start;
     const float *__restrict__ dec;
     const float2 *__restrict__ tw;
     int *counter;
     long long total;
     int nbins, nq, ntheta, nos, Lq, cq, ngroup;
-    float beta, scale;
+    float scale;
+    float phimax;    // max over positions of sum_i phi_i (spread bound)
+    EsPoly poly;     // kernel-parameter (constant) bank: broadcast FMA operands
 };
 
+// a / d for 0 <= a < 2^20, d < 2^10, by a float reciprocal and one correction.
+__device__ __forceinline__ int fast_div(int a, int d, float inv_d) {
+    int q = __float2int_rz(((float)a + 0.5f) * inv_d);
+    const int r = a - q * d;
+    if (r < 0) --q;
+    else if (r >= d) ++q;
+    return q;
+}
+
 template <int W>
-__global__ void __launch_bounds__(kThreadsSlice)
-slice_fwd_kernel(SliceArgs a, const float2 *__restrict__ X, float2 *__restrict__ Y) {
-    extern __shared__ float2 G[];
+__global__ void __launch_bounds__(kThreadsSlice, 2)
+slice_fwd_kernel(const SliceArgs a, const float2 *__restrict__ X, float2 *__restrict__ Y) {
+    extern __shared__ float4 smem_f4[];
+    float2 *G = reinterpret_cast<float2 *>(smem_f4);
     __shared__ long long s_item;
-    const int ldg = padded_len(a.nos);
+    const int ldg = ld_interleaved(a.nos);
     const int mask = a.nos - 1;
     const int extra = a.ngroup > 1 ? 1 : 0;
     for (;;) {
@@ -48,26 +66,25 @@ slice_fwd_kernel(SliceArgs a, const float2 *__restrict__ X, float2 *__restrict__
         const int ncolj = g.nj + extra;
 
         // deapodised, centred columns into bit-reversed grid positions
+        // (grid point u holds column entry l = (u + cq) mod nos when l < nq)
         const float2 *Xk = X + g.x_off + (long long)k * a.nq * a.ntheta;
-        for (int idx = threadIdx.x; idx < ncolj * a.nq; idx += blockDim.x) {
-            const int jj = idx % ncolj;
-            const int l = idx / ncolj;
-            int j = g.ja + jj;
-            if (j >= a.ntheta) j -= a.ntheta;
-            const float2 x = __ldg(Xk + (long long)l * a.ntheta + j);
-            const float dl = __ldg(a.dec + l);
-            const int u = (l - a.cq) & mask;
-            G[jj * ldg + padi(brev_bits(u, a.Lq))] = make_float2(x.x * dl, x.y * dl);
-        }
-        const int nz = a.nos - a.nq;
-        for (int idx = threadIdx.x; idx < ncolj * nz; idx += blockDim.x) {
-            const int jj = idx % ncolj;
-            const int i = idx / ncolj;
-            const int u = (a.nq - a.cq + i) & mask;
-            G[jj * ldg + padi(brev_bits(u, a.Lq))] = make_float2(0.f, 0.f);
+        const float inv_nc = 1.0f / (float)ncolj;
+        for (int idx = threadIdx.x; idx < ncolj * a.nos; idx += blockDim.x) {
+            const int u = fast_div(idx, ncolj, inv_nc);
+            const int jj = idx - u * ncolj;
+            const int l = (u + a.cq) & mask;
+            float2 v = make_float2(0.f, 0.f);
+            if (l < a.nq) {
+                int j = g.ja + jj;
+                if (j >= a.ntheta) j -= a.ntheta;
+                const float2 x = __ldg(Xk + (long long)l * a.ntheta + j);
+                const float dl = __ldg(a.dec + l);
+                v = make_float2(x.x * dl, x.y * dl);
+            }
+            G[jj * ldg + padi(brev_bits(u, a.Lq))] = v;
         }
         __syncthreads();
-        block_fft_dit<false>(G, ldg, ncolj, a.Lq, a.tw);
+        block_fft<false, false>(IBatch{G, ldg}, ncolj, a.Lq, a.tw);
 
         // interpolate every owned trace
         const TraceGeo *geo = a.geo + g.geo_off;
@@ -76,7 +93,7 @@ slice_fwd_kernel(SliceArgs a, const float2 *__restrict__ X, float2 *__restrict__
             const TraceGeo tr = geo[t];
             const TapSet ts = trace_taps<W>(tr.A, tr.B, (unsigned)k, a.Lq);
             float phi[W];
-            es_weights<W>(ts.z0, a.beta, phi);
+            es_weights<W>(a.poly, ts.g, phi);
             const int jj0 = tr.j0 - g.ja;
             int jj1;
             if (extra) {
@@ -87,17 +104,20 @@ slice_fwd_kernel(SliceArgs a, const float2 *__restrict__ X, float2 *__restrict__
             }
             const float2 *G0 = G + jj0 * ldg;
             const float2 *G1 = G + jj1 * ldg;
-            float ar = 0.f, ai = 0.f;
+            float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
 #pragma unroll
             for (int i = 0; i < W; ++i) {
                 const int u = padi((ts.u0 + i) & mask);
                 const float2 g0 = G0[u], g1 = G1[u];
-                const float c0 = phi[i] * tr.w0, c1 = phi[i] * tr.w1;
-                ar = fmaf(c0, g0.x, fmaf(c1, g1.x, ar));
-                ai = fmaf(c0, g0.y, fmaf(c1, g1.y, ai));
+                ar = fmaf(phi[i], g0.x, ar);
+                ai = fmaf(phi[i], g0.y, ai);
+                br = fmaf(phi[i], g1.x, br);
+                bi = fmaf(phi[i], g1.y, bi);
             }
+            ar = fmaf(tr.w0, ar, tr.w1 * br);
+            ai = fmaf(tr.w0, ai, tr.w1 * bi);
             float sn, cs;
-            sincospif(2.0f * ts.ph, &sn, &cs);
+            phase_cs(ts.ph, &sn, &cs);
             // times exp(-2 pi i ph) = cs - i sn
             Yk[tr.col] = make_float2(a.scale * (ar * cs + ai * sn), a.scale * (ai * cs - ar * sn));
         }
@@ -107,14 +127,15 @@ slice_fwd_kernel(SliceArgs a, const float2 *__restrict__ X, float2 *__restrict__
 
 template <int W>
 __device__ __forceinline__ void spread_trace(const SliceArgs &a, const SliceGroup &g,
-                                             const TraceGeo &tr, const float2 *Yk,
-                                             int k, float2 *G, int ldg, int mask) {
+                                             const TraceGeo &tr, const float2 *Yk, int k,
+                                             int *Gre, int *Gim, int lds, int mask,
+                                             const float *fx) {
     const TapSet ts = trace_taps<W>(tr.A, tr.B, (unsigned)k, a.Lq);
     float phi[W];
-    es_weights<W>(ts.z0, a.beta, phi);
+    es_weights<W>(a.poly, ts.g, phi);
     const float2 y = __ldg(Yk + tr.col);
     float sn, cs;
-    sincospif(2.0f * ts.ph, &sn, &cs);
+    phase_cs(ts.ph, &sn, &cs);
     // scale * y * exp(+2 pi i ph)
     const float vr = a.scale * (y.x * cs - y.y * sn);
     const float vi = a.scale * (y.x * sn + y.y * cs);
@@ -124,30 +145,33 @@ __device__ __forceinline__ void spread_trace(const SliceArgs &a, const SliceGrou
     const int jj1 = j1 - g.ja;
     const bool own0 = jj0 >= 0 && jj0 < g.nj;
     const bool own1 = jj1 >= 0 && jj1 < g.nj;
-    float *G0 = reinterpret_cast<float *>(G + (own0 ? jj0 : 0) * ldg);
-    float *G1 = reinterpret_cast<float *>(G + (own1 ? jj1 : 0) * ldg);
+    const int c0 = own0 ? jj0 : 0, c1 = own1 ? jj1 : 0;
+    const int o0 = c0 * lds, o1 = c1 * lds;
+    const float f0 = tr.w0 * fx[c0], f1 = tr.w1 * fx[c1];
+    const float ar = f0 * vr, ai = f0 * vi, br = f1 * vr, bi = f1 * vi;
 #pragma unroll
     for (int i = 0; i < W; ++i) {
-        const int u = 2 * padi((ts.u0 + i) & mask);
+        const int u = padi((ts.u0 + i) & mask);
         if (own0) {
-            const float c = phi[i] * tr.w0;
-            atomicAdd(G0 + u, c * vr);
-            atomicAdd(G0 + u + 1, c * vi);
+            atomicAdd(Gre + o0 + u, __float2int_rn(phi[i] * ar));
+            atomicAdd(Gim + o0 + u, __float2int_rn(phi[i] * ai));
         }
         if (own1) {
-            const float c = phi[i] * tr.w1;
-            atomicAdd(G1 + u, c * vr);
-            atomicAdd(G1 + u + 1, c * vi);
+            atomicAdd(Gre + o1 + u, __float2int_rn(phi[i] * br));
+            atomicAdd(Gim + o1 + u, __float2int_rn(phi[i] * bi));
         }
     }
 }
 
 template <int W>
-__global__ void __launch_bounds__(kThreadsSlice)
-slice_adj_kernel(SliceArgs a, const float2 *__restrict__ Y, float2 *__restrict__ X) {
-    extern __shared__ float2 G[];
+__global__ void __launch_bounds__(kThreadsSlice, 2)
+slice_adj_kernel(const SliceArgs a, const float2 *__restrict__ Y, float2 *__restrict__ X) {
+    extern __shared__ float4 smem_f4[];
+    float *smf = reinterpret_cast<float *>(smem_f4);
     __shared__ long long s_item;
-    const int ldg = padded_len(a.nos);
+    __shared__ float s_sa[kMaxGroupSlices + 1], s_sb[kMaxGroupSlices + 1];
+    __shared__ float s_fx[kMaxGroupSlices];
+    const int lds = ld_split(a.nos);
     const int mask = a.nos - 1;
     for (;;) {
         if (threadIdx.x == 0) s_item = (long long)atomicAdd(a.counter, 1);
@@ -157,28 +181,83 @@ slice_adj_kernel(SliceArgs a, const float2 *__restrict__ Y, float2 *__restrict__
         const int gi = (int)(item / a.nbins);
         const int k = (int)(item - (long long)gi * a.nbins);
         const SliceGroup g = a.groups[gi];
-
-        for (int idx = threadIdx.x; idx < g.nj * ldg; idx += blockDim.x)
-            G[idx] = make_float2(0.f, 0.f);
-        __syncthreads();
-
+        float *Gre = smf;
+        float *Gim = smf + g.nj * lds;
+        int *Ire = reinterpret_cast<int *>(Gre);
+        int *Iim = reinterpret_cast<int *>(Gim);
         const TraceGeo *geo = a.geo + g.geo_off;
         const float2 *Yk = Y + g.y_off + (long long)k * g.ntr;
-        for (int t = g.f0 + threadIdx.x; t < g.f1; t += blockDim.x)
-            spread_trace<W>(a, g, geo[t], Yk, k, G, ldg, mask);
-        for (int t = g.e0 + threadIdx.x; t < g.e1; t += blockDim.x)
-            spread_trace<W>(a, g, geo[t], Yk, k, G, ldg, mask);
+
+        // zero the grid; per owned slice, bound its spread by the sums
+        // A_j = sum w0 |y| over traces with j0 = j and B_j = sum w1 |y| over
+        // traces with j0 = j (whose second weight lands on slice j + 1)
+        for (int idx = threadIdx.x; idx < 2 * g.nj * lds; idx += blockDim.x) smf[idx] = 0.f;
+        const int *sstart = a.slice_start + g.ss_off;
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int nseg = g.nj + 1;            // owned slices, then the slice before ja
+        for (int sg = warp; sg < nseg; sg += kThreadsSlice / 32) {
+            int t0, t1;
+            if (sg < g.nj) {
+                t0 = sstart[g.ja + sg];
+                t1 = sstart[g.ja + sg + 1];
+            } else {
+                t0 = g.e0;                   // empty when one group owns every slice
+                t1 = g.e1;
+            }
+            float sa = 0.f, sb = 0.f;
+            for (int t = t0 + lane; t < t1; t += 32) {
+                const TraceGeo tr = geo[t];
+                const float2 y = __ldg(Yk + tr.col);
+                const float ay = fabsf(y.x) + fabsf(y.y);
+                sa = fmaf(tr.w0, ay, sa);
+                sb = fmaf(tr.w1, ay, sb);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                sa += __shfl_down_sync(0xffffffffu, sa, o);
+                sb += __shfl_down_sync(0xffffffffu, sb, o);
+            }
+            if (lane == 0) {
+                s_sa[sg] = sa;
+                s_sb[sg] = sb;
+            }
+        }
         __syncthreads();
-        block_fft_dif<true>(G, ldg, g.nj, a.Lq, a.tw);
+        for (int jj = threadIdx.x; jj < g.nj; jj += blockDim.x) {
+            // slice jj receives w1 parts from the slice before it: jj - 1, or
+            // for jj = 0 the slice before the group (last owned slice when the
+            // group owns every slice, else the e-range)
+            const float prev = jj > 0 ? s_sb[jj - 1] : (a.ngroup > 1 ? s_sb[g.nj] : s_sb[g.nj - 1]);
+            const float bound = (s_sa[jj] + prev) * a.scale * a.phimax;
+            s_fx[jj] = bound > 0.f ? 1073741824.0f / bound : 0.f;   // 2^30 / bound
+        }
+        __syncthreads();
+
+        for (int t = g.f0 + threadIdx.x; t < g.f1; t += blockDim.x)
+            spread_trace<W>(a, g, geo[t], Yk, k, Ire, Iim, lds, mask, s_fx);
+        for (int t = g.e0 + threadIdx.x; t < g.e1; t += blockDim.x)
+            spread_trace<W>(a, g, geo[t], Yk, k, Ire, Iim, lds, mask, s_fx);
+        __syncthreads();
+        // back to floating point, in place (slice jj sits in rows jj and nj + jj)
+        const float inv_lds = 1.0f / (float)lds;
+        for (int idx = threadIdx.x; idx < 2 * g.nj * lds; idx += blockDim.x) {
+            int jj = fast_div(idx, lds, inv_lds);
+            if (jj >= g.nj) jj -= g.nj;
+            const float f = s_fx[jj];
+            smf[idx] = f > 0.f ? (float)reinterpret_cast<int *>(smf)[idx] / f : 0.f;
+        }
+        __syncthreads();
+        block_fft<true, true>(SBatch{Gre, Gim, lds}, g.nj, a.Lq, a.tw);
 
         float2 *Xk = X + g.x_off + (long long)k * a.nq * a.ntheta;
+        const float inv_nj = 1.0f / (float)g.nj;
         for (int idx = threadIdx.x; idx < g.nj * a.nq; idx += blockDim.x) {
-            const int jj = idx % g.nj;
-            const int l = idx / g.nj;
-            const int u = (l - a.cq) & mask;
-            const float2 v = G[jj * ldg + padi(brev_bits(u, a.Lq))];
+            const int l = fast_div(idx, g.nj, inv_nj);
+            const int jj = idx - l * g.nj;
+            const int u = padi(brev_bits((l - a.cq) & mask, a.Lq));
             const float dl = __ldg(a.dec + l);
-            Xk[(long long)l * a.ntheta + g.ja + jj] = make_float2(v.x * dl, v.y * dl);
+            Xk[(long long)l * a.ntheta + g.ja + jj] =
+                make_float2(Gre[jj * lds + u] * dl, Gim[jj * lds + u] * dl);
         }
         __syncthreads();
     }
@@ -188,6 +267,7 @@ static SliceArgs make_args(const Plan &p, int counter_slot) {
     SliceArgs a;
     a.geo = p.geo;
     a.groups = p.groups;
+    a.slice_start = p.slice_start;
     a.dec = p.dec;
     a.tw = p.tw_q;
     a.counter = p.counters + counter_slot;
@@ -199,8 +279,9 @@ static SliceArgs make_args(const Plan &p, int counter_slot) {
     a.Lq = p.Lq;
     a.cq = p.cq;
     a.ngroup = p.ngroup;
-    a.beta = (float)p.beta;
     a.scale = (float)(1.0 / p.nfft);
+    a.phimax = (float)p.phimax;
+    a.poly = p.poly;
     return a;
 }
 
@@ -243,20 +324,14 @@ cudaError_t launch_slice(Plan &p, bool adjoint, const float2 *in, float2 *out,
 }
 
 // Dynamic shared memory attributes and persistent grid sizes for width w.
-cudaError_t configure_slice_kernels(Plan &p, int num_sms) {
+cudaError_t configure_slice_kernels(Plan &p, int num_sms, int max_smem) {
     cudaError_t e = cudaSuccess;
     int occ_f = 0, occ_a = 0;
     switch (p.w) {
 #define AAHRT_CASE(WW)                                                                   \
     case WW:                                                                            \
-        if ((e = cudaFuncSetAttribute(slice_fwd_kernel<WW>,                              \
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize,       \
-                                      (int)p.smem_sfwd)))                                \
-            return e;                                                                   \
-        if ((e = cudaFuncSetAttribute(slice_adj_kernel<WW>,                              \
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize,       \
-                                      (int)p.smem_sadj)))                                \
-            return e;                                                                   \
+        if ((e = raise_smem_limit(slice_fwd_kernel<WW>, max_smem))) return e;            \
+        if ((e = raise_smem_limit(slice_adj_kernel<WW>, max_smem))) return e;            \
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(                          \
                  &occ_f, slice_fwd_kernel<WW>, kThreadsSlice, p.smem_sfwd)))             \
             return e;                                                                   \

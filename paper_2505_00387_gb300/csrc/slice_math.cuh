@@ -14,18 +14,33 @@
 // phi(z) = exp(beta (sqrt(1 - (2z/W)^2) - 1)), |z| <= W/2.  The total phase
 // per bin is frac(k A) and the position frac(k B) (A, B: 0.64 fixed point),
 // so both are exact integer products modulo 2^64.
+//
+// Tap i of a trace sits at distance z_i = g + (W-1)/2 - i from the position,
+// g in [-1/2, 1/2); phi_i(g) = phi(g + (W-1)/2 - i) is evaluated as a
+// degree-(W+1) polynomial in g per tap (Horner), fitted on the host.
 #pragma once
 
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstring>
+#include <utility>
+#include <vector>
 
 namespace aahrt {
 
+constexpr int kPolyMaxW = 12;
+constexpr int kPolyMaxD = kPolyMaxW + 1;
+
+// c[d][i]: coefficient of g^d of tap i.
+struct EsPoly {
+    float c[kPolyMaxD + 1][kPolyMaxW];
+};
+
 struct TapSet {
     int u0;      // first grid point (may be negative; index mod nos)
-    float z0;    // distance (grid units) from the first tap to the position
-    float ph;    // phase in cycles, [-0.5, 0.5)
+    float g;     // centred offset of the position, [-1/2, 1/2)
+    float ph;    // phase in cycles, [-1/2, 1/2)
 };
 
 template <int W>
@@ -40,27 +55,71 @@ __host__ __device__ __forceinline__ TapSet trace_taps(unsigned long long A,
     t.ph = (float)(int)ptop * 2.3283064365386963e-10f;      // 2^-32
     const int iu = (int)(xtop >> (32 - Lq));                  // integer part of nos*x
     const float fy = (float)(unsigned)(xtop << Lq) * 2.3283064365386963e-10f;
-    if (W & 1)
-        t.u0 = iu - (W - 1) / 2 + (fy >= 0.5f ? 1 : 0);
-    else
+    if (W & 1) {
+        const bool up = fy >= 0.5f;
+        t.u0 = iu - (W - 1) / 2 + (up ? 1 : 0);
+        t.g = up ? fy - 1.0f : fy;
+    } else {
         t.u0 = iu - W / 2 + 1;
-    t.z0 = (float)(iu - t.u0) + fy;
+        t.g = fy - 0.5f;
+    }
     return t;
 }
 
-// phi at the W taps u0 + i, i < W (distance z0 - i).
+// phi at the W taps u0 + i, i < W.
 template <int W>
-__host__ __device__ __forceinline__ void es_weights(float z0, float beta, float *phi) {
-    const float inv = 2.0f / (float)W;
+__host__ __device__ __forceinline__ void es_weights(const EsPoly &P, float g, float *phi) {
+    constexpr int D = W + 1;
 #pragma unroll
-    for (int i = 0; i < W; ++i) {
-        const float t = (z0 - (float)i) * inv;
-        const float s = fmaxf(1.0f - t * t, 0.0f);
+    for (int i = 0; i < W; ++i) phi[i] = P.c[D][i];
+#pragma unroll
+    for (int d = D - 1; d >= 0; --d) {
+#pragma unroll
+        for (int i = 0; i < W; ++i) phi[i] = fmaf(phi[i], g, P.c[d][i]);
+    }
+}
+
+// exp(-2 pi i ph) as (cos, -sin) parts: returns c = cos(2 pi ph), s = sin(2 pi ph)
+__host__ __device__ __forceinline__ void phase_cs(float ph, float *s, float *c) {
 #ifdef __CUDA_ARCH__
-        phi[i] = __expf(beta * (sqrtf(s) - 1.0f));
+    __sincosf(6.28318530717958647692f * ph, s, c);
 #else
-        phi[i] = expf(beta * (sqrtf(s) - 1.0f));
+    *s = sinf(6.28318530717958647692f * ph);
+    *c = cosf(6.28318530717958647692f * ph);
 #endif
+}
+
+// Per-tap polynomial of the spreading kernel: phi_i(g) = phi(g + (W-1)/2 - i)
+// for g in [-1/2, 1/2], interpolated at D+1 Chebyshev points (D = W+1) and
+// written in the monomial basis of g (small Vandermonde solve in FP64).
+inline void fit_es_poly(int W, double beta, EsPoly *P) {
+    std::memset(P, 0, sizeof *P);
+    const int D = W + 1;
+    const int n = D + 1;
+    std::vector<double> xs(n);
+    for (int k = 0; k < n; ++k) xs[k] = 0.5 * std::cos(M_PI * (k + 0.5) / n);
+    for (int i = 0; i < W; ++i) {
+        std::vector<double> A((size_t)n * (n + 1));
+        for (int r = 0; r < n; ++r) {
+            double pw = 1.0;
+            for (int c = 0; c < n; ++c) { A[r * (n + 1) + c] = pw; pw *= xs[r]; }
+            const double z = xs[r] + 0.5 * (W - 1) - i;
+            const double t = 2.0 * z / W;
+            const double s = 1.0 - t * t;
+            A[r * (n + 1) + n] = s > 0.0 ? std::exp(beta * (std::sqrt(s) - 1.0)) : 0.0;
+        }
+        for (int c = 0; c < n; ++c) {   // Gaussian elimination, partial pivoting
+            int piv = c;
+            for (int r = c + 1; r < n; ++r)
+                if (std::fabs(A[r * (n + 1) + c]) > std::fabs(A[piv * (n + 1) + c])) piv = r;
+            for (int q = 0; q <= n; ++q) std::swap(A[c * (n + 1) + q], A[piv * (n + 1) + q]);
+            for (int r = 0; r < n; ++r) {
+                if (r == c) continue;
+                const double f = A[r * (n + 1) + c] / A[c * (n + 1) + c];
+                for (int q = c; q <= n; ++q) A[r * (n + 1) + q] -= f * A[c * (n + 1) + q];
+            }
+        }
+        for (int d = 0; d < n; ++d) P->c[d][i] = (float)(A[d * (n + 1) + n] / A[d * (n + 1) + d]);
     }
 }
 

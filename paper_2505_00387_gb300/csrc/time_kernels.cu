@@ -1,60 +1,156 @@
 // Time-axis stages of the AAHRT (Algorithms 1 and 2, steps 1-2 and 4-5):
 //
 //   r2c: X[k][c] = sum_n (G in)[n][c] exp(-2 pi i k n / Nfft), k < nbins
-//        where G is a sparse resampler applied to each column: the time
-//        stretch S (model side, Alg. 1 steps 1-2) or the transpose of its
-//        undoing U^T (data side, the adjoint's first two stages).
+//        where G resamples each column: the time stretch S (model side,
+//        Alg. 1 steps 1-2) or the transpose of its undoing, U^T (data side,
+//        the adjoint's first two stages).
 //   c2r: out[i][c] = sum_n G[i][n] H(X[.][c])[n] with the band-limited
 //        Hermitian synthesis H(X)[n] = Re X_0 + 2 Re sum_{k>=1} X_k e^{+2 pi i k n/Nfft}
 //        and G = U (data side, Alg. 1 steps 4-5) or S^T (model side, the
 //        adjoint's last two stages).  Epilogues fuse the FISTA residual
 //        r = d - L z and the soft-threshold/momentum update (eqs. ISTA, soft).
 //
-// One block owns up to 2*pairs adjacent columns; two real columns travel as
+// One block owns up to 2*P adjacent columns; two real columns travel as
 // the real and imaginary parts of one complex FFT of length Nfft held in
-// shared memory (padded layout of fft.cuh).  The resampler rows are CSR
-// (row pointer, input index, weight) shared by every column.
+// shared memory (padded layout of fft.cuh).  Each thread resamples whole
+// rows (all P pairs), so a row's weights are computed once per block.
+//
+// Resampling: output row o of S (or U) sits at position fl + fr on the input
+// axis and reads input rows fl + t with weight kern(fr - t), t in the kernel's
+// taps.  The transposed operators read, for output o, the contiguous source
+// rows of a host-built table, in segments of equal tap t, and recompute the
+// same weight from the source row's fr through the same function, so S and
+// S^T (U and U^T) use bit-identical weights.
 #include "fft.cuh"
 #include "internal.cuh"
 
 namespace aahrt {
 
-__global__ void __launch_bounds__(kThreadsTime)
+// Weights of the interpolation kernel at the taps of a position fl + x,
+// x in [0, 1): tap t (input row fl + t) gets kern(x - t).  Keys' cubic
+// convolution (a = -1/2) has taps t = -1..2 with the branch-free forms
+//   c(x+1) = ((-x/2 + 1) x - 1/2) x,   c(x)   = (3x/2 - 5/2) x^2 + 1,
+//   c(x-1) = ((-3x/2 + 2) x + 1/2) x,  c(x-2) = (x/2 - 1/2) x^2,
+// linear interpolation taps t = 0, 1 with 1 - x and x.
+template <int INTERP> struct Taps;
+template <> struct Taps<AAHRT_INTERP_KEYS> { static constexpr int t0 = -1, n = 4; };
+template <> struct Taps<AAHRT_INTERP_LINEAR> { static constexpr int t0 = 0, n = 2; };
+
+template <int INTERP>
+__device__ __forceinline__ float tap_weight(int t, float x) {
+    if (INTERP == AAHRT_INTERP_LINEAR) return t == 0 ? __fadd_rn(1.0f, -x) : x;
+    switch (t) {
+        case -1: return __fmul_rn(__fmaf_rn(__fmaf_rn(-0.5f, x, 1.0f), x, -0.5f), x);
+        case 0: return __fmaf_rn(__fmaf_rn(1.5f, x, -2.5f), __fmul_rn(x, x), 1.0f);
+        case 1: return __fmul_rn(__fmaf_rn(__fmaf_rn(-1.5f, x, 2.0f), x, 0.5f), x);
+        default: return __fmul_rn(__fmaf_rn(0.5f, x, -0.5f), __fmul_rn(x, x));
+    }
+}
+
+__device__ __forceinline__ RowPos load_pos(const RowPos *p) {
+    const int2 v = __ldg(reinterpret_cast<const int2 *>(p));
+    return RowPos{v.x, __int_as_float(v.y)};
+}
+// Transposed row: sources lo, lo+1, ... in segments of decreasing tap t
+// (largest t first); segment q (tap t0 + q) has (cnt >> 8q) & 255 rows.
+__device__ __forceinline__ RowRange load_rng(const RowRange *p) {
+    const int2 v = __ldg(reinterpret_cast<const int2 *>(p));
+    return RowRange{v.x, v.y};
+}
+
+template <int P>
+struct Acc {
+    float2 v[P];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int p = 0; p < P; ++p) v[p] = make_float2(0.f, 0.f);
+    }
+    // += w * (P complex values at row r of a row-major [row][P] float2 array)
+    __device__ __forceinline__ void add_row(float w, const float2 *row) {
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const float2 x = row[p];
+            v[p].x = fmaf(w, x.x, v[p].x);
+            v[p].y = fmaf(w, x.y, v[p].y);
+        }
+    }
+    // += w * (column p at padded position pr of P sequences ld apart)
+    __device__ __forceinline__ void add_cols(float w, const float2 *sm, int ld, int pr) {
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const float2 x = sm[p * ld + pr];
+            v[p].x = fmaf(w, x.x, v[p].x);
+            v[p].y = fmaf(w, x.y, v[p].y);
+        }
+    }
+};
+
+template <int LP, int INTERP, bool TRANS>
+__global__ void __launch_bounds__(kThreadsTime, 2)
 r2c_kernel(const float *__restrict__ in, float2 *__restrict__ out,
-           const ColGroup *__restrict__ groups, DevCSR gat,
+           const ColGroup *__restrict__ groups, DevResampler rs, int nrow_in,
            const float2 *__restrict__ tw, int L, int nbins) {
-    extern __shared__ float2 sm[];
+    constexpr int P = 1 << LP;
+    extern __shared__ float4 smem_f4[];
+    float2 *sm = reinterpret_cast<float2 *>(smem_f4);
     const ColGroup cg = groups[blockIdx.x];
     const int N = 1 << L;
-    const int ld = padded_len(N);
-    const int P = (cg.ncol + 1) >> 1;
-    const float *src = in + cg.real_off;
+    const int ld = ld_interleaved(N);
+    float *stg = reinterpret_cast<float *>(sm + P * ld);          // staged input [row][2P]
+    float *sfr = stg + nrow_in * 2 * P;                           // source fractions (TRANS)
 
-    // gather: z_p[n] = sum_e val[e] * (src[col[e]][2p] + i src[col[e]][2p+1])
-    for (int idx = threadIdx.x; idx < P * N; idx += blockDim.x) {
-        const int p = idx % P;
-        const int n = idx / P;
-        float zr = 0.f, zi = 0.f;
-        if (n < gat.nrows) {
-            const int e0 = __ldg(gat.rowptr + n), e1 = __ldg(gat.rowptr + n + 1);
-            const bool hasb = 2 * p + 1 < cg.ncol;
-            for (int e = e0; e < e1; ++e) {
-                const float wv = __ldg(gat.val + e);
-                const float *rowp = src + (long long)__ldg(gat.col + e) * cg.ld_real + 2 * p;
-                zr = fmaf(wv, __ldg(rowp), zr);
-                if (hasb) zi = fmaf(wv, __ldg(rowp + 1), zi);
+    // stage the block's input columns (independent, coalesced loads)
+    const float *src = in + cg.real_off;
+    for (int idx = threadIdx.x; idx < nrow_in * 2 * P; idx += blockDim.x) {
+        const int r = idx >> (LP + 1);
+        const int c = idx & (2 * P - 1);
+        stg[idx] = c < cg.ncol ? __ldg(src + (long long)r * cg.ld_real + c) : 0.f;
+    }
+    if (TRANS)
+        for (int idx = threadIdx.x; idx < rs.npos; idx += blockDim.x)
+            sfr[idx] = __ldg(&rs.pos[idx].fr);
+    __syncthreads();
+
+    // z_p[n] = sum_r G[n][r] (x_{2p} + i x_{2p+1})[r], one row n per thread
+    const float2 *stg2 = reinterpret_cast<const float2 *>(stg);
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+        Acc<P> acc;
+        acc.zero();
+        if (n < rs.nrows) {
+            if (!TRANS) {
+                const RowPos ps = load_pos(rs.pos + n);
+#pragma unroll
+                for (int q = 0; q < Taps<INTERP>::n; ++q) {
+                    const int t = Taps<INTERP>::t0 + q;
+                    const int r = ps.fl + t;
+                    if (r < 0 || r >= nrow_in) continue;
+                    acc.add_row(tap_weight<INTERP>(t, ps.fr), stg2 + r * P);
+                }
+            } else {
+                const RowRange rg = load_rng(rs.rng + n);
+                int r = rg.lo;
+#pragma unroll
+                for (int q = Taps<INTERP>::n - 1; q >= 0; --q) {
+                    const int t = Taps<INTERP>::t0 + q;
+                    const int cnt = (rg.cnt >> (8 * q)) & 255;
+                    for (int e = 0; e < cnt; ++e, ++r)
+                        acc.add_row(tap_weight<INTERP>(t, sfr[r]), stg2 + r * P);
+                }
             }
         }
-        sm[p * ld + padi(n)] = make_float2(zr, zi);
+#pragma unroll
+        for (int p = 0; p < P; ++p) sm[p * ld + padi(n)] = acc.v[p];
     }
     __syncthreads();
-    block_fft_dif<false>(sm, ld, P, L, tw);
+    block_fft<true, false>(IBatch{sm, ld}, P, L, tw);
 
     // unpack the two real spectra: A = (Z_k + conj Z_{N-k})/2, B = (Z_k - conj Z_{N-k})/(2i)
     float2 *dst = out + cg.spec_off;
+    const int npair = (cg.ncol + 1) >> 1;
     for (int idx = threadIdx.x; idx < P * nbins; idx += blockDim.x) {
-        const int p = idx % P;
-        const int k = idx / P;
+        const int p = idx & (P - 1);
+        const int k = idx >> LP;
+        if (p >= npair) continue;
         const float2 zk = sm[p * ld + padi(brev_bits(k, L))];
         const float2 zn = sm[p * ld + padi(brev_bits((N - k) & (N - 1), L))];
         const float2 A = make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
@@ -70,26 +166,32 @@ __device__ __forceinline__ float soft_threshold(float x, float t) {
     return copysignf(fmaxf(fabsf(x) - t, 0.f), x);
 }
 
-template <int EPI>
-__global__ void __launch_bounds__(kThreadsTime)
+template <int LP, int INTERP, bool TRANS, int EPI>
+__global__ void __launch_bounds__(kThreadsTime, 2)
 c2r_kernel(const float2 *__restrict__ in, float *__restrict__ out,
            const float *__restrict__ aux, FistaArgs fa,
-           const ColGroup *__restrict__ groups, DevCSR gat,
+           const ColGroup *__restrict__ groups, DevResampler rs, int n_in,
            const float2 *__restrict__ tw, int L, int nbins) {
-    extern __shared__ float2 sm[];
+    constexpr int P = 1 << LP;
+    extern __shared__ float4 smem_f4[];
+    float2 *sm = reinterpret_cast<float2 *>(smem_f4);
     const ColGroup cg = groups[blockIdx.x];
     const int N = 1 << L;
     const int half = N >> 1;
-    const int ld = padded_len(N);
-    const int P = (cg.ncol + 1) >> 1;
+    const int ld = ld_interleaved(N);
+    float *sfr = reinterpret_cast<float *>(sm + P * ld);
     const float2 *src = in + cg.spec_off;
+    const int npair = (cg.ncol + 1) >> 1;
 
+    if (TRANS)
+        for (int idx = threadIdx.x; idx < rs.npos; idx += blockDim.x)
+            sfr[idx] = __ldg(&rs.pos[idx].fr);
     // pack Z = A + iB over the full frame, bit-reversed for the DIT pass
     for (int idx = threadIdx.x; idx < P * (half + 1); idx += blockDim.x) {
-        const int p = idx % P;
-        const int k = idx / P;
+        const int p = idx & (P - 1);
+        const int k = idx >> LP;
         float2 zk = make_float2(0.f, 0.f), zn = zk;
-        if (k < nbins) {
+        if (k < nbins && p < npair) {
             const long long o = (long long)k * cg.ld_spec + 2 * p;
             float2 A = __ldg(src + o);
             float2 B = (2 * p + 1 < cg.ncol) ? __ldg(src + o + 1) : make_float2(0.f, 0.f);
@@ -108,52 +210,120 @@ c2r_kernel(const float2 *__restrict__ in, float *__restrict__ out,
         }
     }
     __syncthreads();
-    block_fft_dit<true>(sm, ld, P, L, tw);
+    block_fft<false, true>(IBatch{sm, ld}, P, L, tw);
 
-    // resample the synthesized columns onto the output rows
-    for (int idx = threadIdx.x; idx < P * gat.nrows; idx += blockDim.x) {
-        const int p = idx % P;
-        const int i = idx / P;
-        const int e0 = __ldg(gat.rowptr + i), e1 = __ldg(gat.rowptr + i + 1);
-        float va = 0.f, vb = 0.f;
-        for (int e = e0; e < e1; ++e) {
-            const float wv = __ldg(gat.val + e);
-            const float2 z = sm[p * ld + padi(__ldg(gat.col + e))];
-            va = fmaf(wv, z.x, va);
-            vb = fmaf(wv, z.y, vb);
+    // resample the synthesized columns onto the output rows, one row per thread
+    for (int i = threadIdx.x; i < rs.nrows; i += blockDim.x) {
+        Acc<P> acc;
+        acc.zero();
+        if (!TRANS) {
+            const RowPos ps = load_pos(rs.pos + i);
+#pragma unroll
+            for (int q = 0; q < Taps<INTERP>::n; ++q) {
+                const int t = Taps<INTERP>::t0 + q;
+                const int r = ps.fl + t;
+                if (r < 0 || r >= n_in) continue;
+                acc.add_cols(tap_weight<INTERP>(t, ps.fr), sm, ld, padi(r));
+            }
+        } else {
+            const RowRange rg = load_rng(rs.rng + i);
+            int r = rg.lo;
+#pragma unroll
+            for (int q = Taps<INTERP>::n - 1; q >= 0; --q) {
+                const int t = Taps<INTERP>::t0 + q;
+                const int cnt = (rg.cnt >> (8 * q)) & 255;
+                for (int e = 0; e < cnt; ++e, ++r)
+                    acc.add_cols(tap_weight<INTERP>(t, sfr[r]), sm, ld, padi(r));
+            }
         }
-        const long long o = cg.real_off + (long long)i * cg.ld_real + 2 * p;
-        const bool hasb = 2 * p + 1 < cg.ncol;
+        const long long o = cg.real_off + (long long)i * cg.ld_real;
+        const int nc = cg.ncol;
+        float g2[2 * P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            g2[2 * p] = acc.v[p].x;
+            g2[2 * p + 1] = acc.v[p].y;
+        }
         if (EPI == EPI_STORE) {
-            out[o] = va;
-            if (hasb) out[o + 1] = vb;
+#pragma unroll
+            for (int c = 0; c < 2 * P; ++c)
+                if (c < nc) out[o + c] = g2[c];
         } else if (EPI == EPI_RESIDUAL) {
-            out[o] = __ldg(aux + o) - va;
-            if (hasb) out[o + 1] = __ldg(aux + o + 1) - vb;
+            float dv[2 * P];
+#pragma unroll
+            for (int c = 0; c < 2 * P; ++c) dv[c] = c < nc ? __ldg(aux + o + c) : 0.f;
+#pragma unroll
+            for (int c = 0; c < 2 * P; ++c)
+                if (c < nc) out[o + c] = dv[c] - g2[c];
         } else {
             // m+ = soft(z + gamma g, gamma lambda); z+ = m+ + beta (m+ - m)
-            float g[2] = {va, vb};
+            float *__restrict__ mp = fa.m + o;
+            float *__restrict__ zp = fa.z + o;
+            float mo[2 * P], zo[2 * P];
 #pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                if (c == 1 && !hasb) break;
-                const float mo = fa.m[o + c];
-                const float zo = fa.z[o + c];
-                const float mn = soft_threshold(fmaf(fa.gamma, g[c], zo), fa.thresh);
-                fa.m[o + c] = mn;
-                fa.z[o + c] = fmaf(fa.beta, mn - mo, mn);
+            for (int c = 0; c < 2 * P; ++c) {
+                mo[c] = c < nc ? mp[c] : 0.f;
+                zo[c] = c < nc ? zp[c] : 0.f;
+            }
+#pragma unroll
+            for (int c = 0; c < 2 * P; ++c) {
+                if (c >= nc) break;
+                const float mn = soft_threshold(fmaf(fa.gamma, g2[c], zo[c]), fa.thresh);
+                mp[c] = mn;
+                zp[c] = fmaf(fa.beta, mn - mo[c], mn);
             }
         }
     }
 }
 
+// ------------------------------------------------------------- dispatch
+template <int LP, int INTERP>
+static void r2c_launch(bool model_side, int grid, size_t smem, cudaStream_t st, const float *in,
+                       float2 *out, const ColGroup *cg, DevResampler rs, int nrow_in,
+                       const float2 *tw, int L, int nbins) {
+    if (model_side)
+        r2c_kernel<LP, INTERP, false><<<grid, kThreadsTime, smem, st>>>(in, out, cg, rs, nrow_in,
+                                                                        tw, L, nbins);
+    else
+        r2c_kernel<LP, INTERP, true><<<grid, kThreadsTime, smem, st>>>(in, out, cg, rs, nrow_in,
+                                                                       tw, L, nbins);
+}
+
+template <int LP, int INTERP, int EPI>
+static void c2r_launch(bool model_side, int grid, size_t smem, cudaStream_t st,
+                       const float2 *in, float *out, const float *aux, FistaArgs fa,
+                       const ColGroup *cg, DevResampler rs, int n_in, const float2 *tw, int L,
+                       int nbins) {
+    if (model_side)
+        c2r_kernel<LP, INTERP, true, EPI><<<grid, kThreadsTime, smem, st>>>(
+            in, out, aux, fa, cg, rs, n_in, tw, L, nbins);
+    else
+        c2r_kernel<LP, INTERP, false, EPI><<<grid, kThreadsTime, smem, st>>>(
+            in, out, aux, fa, cg, rs, n_in, tw, L, nbins);
+}
+
+#define AAHRT_LP_SWITCH(LPV, STMT)                      \
+    switch (LPV) {                                      \
+        case 0: { constexpr int LPc = 0; STMT; } break; \
+        case 1: { constexpr int LPc = 1; STMT; } break; \
+        case 2: { constexpr int LPc = 2; STMT; } break; \
+        default: { constexpr int LPc = 3; STMT; } break; \
+    }
+#define AAHRT_INTERP_SWITCH(IV, STMT)                                       \
+    if ((IV) == AAHRT_INTERP_LINEAR) { constexpr int IPc = AAHRT_INTERP_LINEAR; STMT; } \
+    else { constexpr int IPc = AAHRT_INTERP_KEYS; STMT; }
+
 cudaError_t launch_r2c(Plan &p, bool model_side, const float *in, float2 *out,
                        cudaStream_t st) {
     const ColGroup *cg = model_side ? p.cg_model : p.cg_data;
     const int n = model_side ? p.ncg_model : p.ncg_data;
-    const DevCSR gat = model_side ? p.S : p.UT;
+    const DevResampler rs = model_side ? p.S : p.UT;
+    const int nrow_in = model_side ? p.ntau : p.nt;
+    const size_t smem = model_side ? p.smem_r2c_model : p.smem_r2c_data;
     const int stage = model_side ? 0 : 3;
     prof_begin(p, stage, st);
-    r2c_kernel<<<n, kThreadsTime, p.smem_r2c, st>>>(in, out, cg, gat, p.tw_t, p.L, p.nbins);
+    AAHRT_LP_SWITCH(p.lp, AAHRT_INTERP_SWITCH(p.interp, (r2c_launch<LPc, IPc>(
+        model_side, n, smem, st, in, out, cg, rs, nrow_in, p.tw_t, p.L, p.nbins))));
     prof_end(p, st);
     p.launches[stage]++;
     return cudaGetLastError();
@@ -163,21 +333,23 @@ cudaError_t launch_c2r(Plan &p, bool model_side, const float2 *in, float *out,
                        int epi, const float *aux, FistaArgs fa, cudaStream_t st) {
     const ColGroup *cg = model_side ? p.cg_model : p.cg_data;
     const int n = model_side ? p.ncg_model : p.ncg_data;
-    const DevCSR gat = model_side ? p.ST : p.U;
+    const DevResampler rs = model_side ? p.ST : p.U;
+    const int n_in = p.ns;
+    const size_t smem = model_side ? p.smem_c2r_model : p.smem_c2r_data;
     const int stage = model_side ? 5 : 2;
     prof_begin(p, stage, st);
     switch (epi) {
         case EPI_RESIDUAL:
-            c2r_kernel<EPI_RESIDUAL><<<n, kThreadsTime, p.smem_c2r, st>>>(
-                in, out, aux, fa, cg, gat, p.tw_t, p.L, p.nbins);
+            AAHRT_LP_SWITCH(p.lp, AAHRT_INTERP_SWITCH(p.interp, (c2r_launch<LPc, IPc, EPI_RESIDUAL>(
+                model_side, n, smem, st, in, out, aux, fa, cg, rs, n_in, p.tw_t, p.L, p.nbins))));
             break;
         case EPI_FISTA:
-            c2r_kernel<EPI_FISTA><<<n, kThreadsTime, p.smem_c2r, st>>>(
-                in, out, aux, fa, cg, gat, p.tw_t, p.L, p.nbins);
+            AAHRT_LP_SWITCH(p.lp, AAHRT_INTERP_SWITCH(p.interp, (c2r_launch<LPc, IPc, EPI_FISTA>(
+                model_side, n, smem, st, in, out, aux, fa, cg, rs, n_in, p.tw_t, p.L, p.nbins))));
             break;
         default:
-            c2r_kernel<EPI_STORE><<<n, kThreadsTime, p.smem_c2r, st>>>(
-                in, out, aux, fa, cg, gat, p.tw_t, p.L, p.nbins);
+            AAHRT_LP_SWITCH(p.lp, AAHRT_INTERP_SWITCH(p.interp, (c2r_launch<LPc, IPc, EPI_STORE>(
+                model_side, n, smem, st, in, out, aux, fa, cg, rs, n_in, p.tw_t, p.L, p.nbins))));
             break;
     }
     prof_end(p, st);
@@ -185,19 +357,23 @@ cudaError_t launch_c2r(Plan &p, bool model_side, const float2 *in, float *out,
     return cudaGetLastError();
 }
 
-cudaError_t set_time_kernel_attrs(size_t smem) {
+template <int LPc, int IPc>
+static cudaError_t attrs_for(int max_smem) {
     cudaError_t e;
-    const int s = (int)smem;
-    if ((e = cudaFuncSetAttribute(r2c_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, s)))
-        return e;
-    if ((e = cudaFuncSetAttribute(c2r_kernel<EPI_STORE>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, s)))
-        return e;
-    if ((e = cudaFuncSetAttribute(c2r_kernel<EPI_RESIDUAL>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, s)))
-        return e;
-    return cudaFuncSetAttribute(c2r_kernel<EPI_FISTA>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+    if ((e = raise_smem_limit(r2c_kernel<LPc, IPc, false>, max_smem))) return e;
+    if ((e = raise_smem_limit(r2c_kernel<LPc, IPc, true>, max_smem))) return e;
+    if ((e = raise_smem_limit(c2r_kernel<LPc, IPc, false, EPI_STORE>, max_smem))) return e;
+    if ((e = raise_smem_limit(c2r_kernel<LPc, IPc, true, EPI_STORE>, max_smem))) return e;
+    if ((e = raise_smem_limit(c2r_kernel<LPc, IPc, false, EPI_RESIDUAL>, max_smem))) return e;
+    if ((e = raise_smem_limit(c2r_kernel<LPc, IPc, true, EPI_RESIDUAL>, max_smem))) return e;
+    if ((e = raise_smem_limit(c2r_kernel<LPc, IPc, false, EPI_FISTA>, max_smem))) return e;
+    return raise_smem_limit(c2r_kernel<LPc, IPc, true, EPI_FISTA>, max_smem);
+}
+
+cudaError_t set_time_kernel_attrs(int lp, int interp, int max_smem) {
+    cudaError_t e = cudaSuccess;
+    AAHRT_LP_SWITCH(lp, AAHRT_INTERP_SWITCH(interp, (e = attrs_for<LPc, IPc>(max_smem))));
+    return e;
 }
 
 }  // namespace aahrt

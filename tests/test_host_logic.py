@@ -31,6 +31,8 @@ def test_fft_groups_match_dft(tmp_path):
 
 
 def test_trace_taps_exact(tmp_path):
+    """Phase and tap position from the 64-bit fixed-point products agree with
+    exact integer arithmetic; the Horner weights agree with the kernel."""
     exe = str(tmp_path / "slice_harness")
     _compile(os.path.join(HERE, "host", "slice_math_harness.cpp"), exe)
     rng = np.random.default_rng(0)
@@ -40,26 +42,27 @@ def test_trace_taps_exact(tmp_path):
         B = int(rng.integers(0, 2**63)) * 2 + int(rng.integers(0, 2))
         k = int(rng.integers(0, 8192))
         Lq = int(rng.integers(4, 10))
-        W = int(rng.integers(4, 9))
-        cases.append((A, B, k, Lq, W))
-    inp = "\n".join("%d %d %d %d %d" % c for c in cases) + "\n"
+        W = int(rng.integers(4, 13))
+        sig = 2.0 ** (Lq) / max(1, int(rng.integers(2 ** (Lq - 2), 2 ** (Lq - 1) + 1)))
+        beta = 0.97 * np.pi * W * (1 - 1 / (2 * sig))
+        cases.append((A, B, k, Lq, W, beta))
+    inp = "\n".join("%d %d %d %d %d %.17g" % c for c in cases) + "\n"
     r = subprocess.run([exe], input=inp, capture_output=True, text=True, check=True)
-    for (A, B, k, Lq, W), line in zip(cases, r.stdout.strip().splitlines()):
+    for (A, B, k, Lq, W, beta), line in zip(cases, r.stdout.strip().splitlines()):
         vals = line.split()
-        u0, z0, ph = int(vals[0]), float(vals[1]), float(vals[2])
+        u0, g, ph = int(vals[0]), float(vals[1]), float(vals[2])
         phi = np.array([float(v) for v in vals[3:]])
-        # exact: phase = frac(k*A/2^64) in [-1/2, 1/2); position y = nos*frac(k*B/2^64)
         pa = (k * A) % 2**64
         ph_exact = (pa >> 32) / 2**32
         if ph_exact >= 0.5:
             ph_exact -= 1.0
         assert abs(ph - ph_exact) < 2e-7
         y = ((k * B) % 2**64 >> 32) / 2**32 * 2**Lq
-        # all taps within half a kernel width of y, first tap is floor(y - W/2) + 1
-        assert u0 == int(np.floor(y - W / 2)) + 1 or abs(y - W / 2 - round(y - W / 2)) < 1e-5
-        assert abs((y - u0) - z0) < 1e-5 * 2**Lq * 2**-20 + 2e-6
-        z = z0 - np.arange(W)
-        assert np.all(np.abs(z) <= W / 2 + 1e-5)
+        assert -0.5 <= g < 0.5
+        # tap i sits at distance z_i = g + (W-1)/2 - i = y - (u0 + i)
+        assert abs((y - u0) - (g + (W - 1) / 2)) < 2e-6 * 2**Lq
+        z = g + (W - 1) / 2 - np.arange(W)
         t = 2 * z / W
-        want = np.exp(2.3 * W * (np.sqrt(np.clip(1 - t * t, 0, None)) - 1))
-        np.testing.assert_allclose(phi, want, rtol=2e-5, atol=2e-6)  # edge taps are ill-conditioned in float
+        want = np.exp(beta * (np.sqrt(np.clip(1 - t * t, 0, None)) - 1))
+        # polynomial fit + float rounding; the edge discontinuity e^-beta bounds it
+        np.testing.assert_allclose(phi, want, rtol=0, atol=2e-6 + 4 * np.exp(-beta))
