@@ -122,7 +122,7 @@ typedef struct {
 } aahrt_plan_info;
 
 /* Create a plan on the current CUDA device: validates the geometry,
- * computes the stretched-time sampling (Sec. 3.3 steps 1-2) and the trace
+ * computes the stretched-time sampling (Sec. 3.4, steps 1-2) and the trace
  * azimuth binning (eq. thli), and allocates the device workspace.  With
  * opts->ngather = G > 1 the plan serves G gathers on this one geometry,
  * stored back to back in m and d.  On success *out owns device memory until

@@ -7,7 +7,7 @@ package.  The CUDA library never uses it and shares no code with it.
 
 What it computes (paper sections and equations):
 
-* ``plan``      sampling of the stretched time axis (Sec. 3.3 step 1, eq. q3)
+* ``plan``      sampling of the stretched time axis (Sec. 3.4 step 1, Sec. 3.5 eq. q3)
                 and the azimuth binning of every trace (eq. thli, theta part).
 * ``ops``       the discrete operator R^{-1} = S^{-1} F1^{-1} P F2 S of
                 eq. axb2 (Algorithm 1) and its exact transpose (the adjoint of
@@ -21,7 +21,7 @@ What it computes (paper sections and equations):
                 momentum variant, power iteration for the step length.
 * ``checks``    independent evaluations used only to pin the oracle: the
                 physical-domain Riemann sum along the azimuth-dependent
-                hyperbolae (eq. Inverse, Sec. 4.1) and the time-domain
+                hyperbolae (eq. Inverse, Sec. 5.1) and the time-domain
                 band-limited shift that the Fourier slice step must equal
                 (the shift theorem behind eq. Inv_op).
 

@@ -4,7 +4,7 @@
     L^T = S^T . F^T . P^H . F1inv^T . U^T  (transpose of every factor; the
                                             paper's adjoint, Sec. 3.2)
 
-S     time stretch tau -> s = tau^2 (Algorithm 1 step 1, Sec. 3.3): the model
+S     time stretch tau -> s = tau^2 (Algorithm 1 step 1, Sec. 3.4): the model
       column is resampled at tau = sqrt(s_n) by a local interpolation kernel.
 U     the stretch undone (step 5, the paper's S^{-1}): the stretched-time data
       are resampled at s = t_i^2.  Both use Keys' cubic convolution

@@ -3,7 +3,7 @@
 Readings of the paper used here (each is listed with its reason in the
 design notes of the repository):
 
-* The curvature axis is uniform, q_l = q0 + l*dq (FFT along q, Sec. 3.3 and
+* The curvature axis is uniform, q_l = q0 + l*dq (FFT along q, Sec. 3.4 and
   eq. q1-q3 need uniform q).
 * The model intercept axis is tau_i = i*dt for i < ntau, the data axis is
   t_i = i*dt for i < nt.
@@ -114,7 +114,7 @@ def azimuth_bins(hx, hy, ntheta):
 
 def make_plan(nt, dt, ntau, nq, q0, dq, ntheta, hx, hy, *, sigma_t=2.0,
               fmax=0.0, interp="keys", r2max=None) -> OraclePlan:
-    """Stretched-time sampling plan (Sec. 3.3, step 1 and 2 of Algorithms 1
+    """Stretched-time sampling plan (Sec. 3.4, step 1 and 2 of Algorithms 1
     and 2) and per-trace geometry.  r2max overrides the largest squared
     offset (a batch of cubes shares one time plan built from the batch-wide
     maximum)."""

@@ -1,6 +1,6 @@
-// Plan construction of libaahrt: stretched-time sampling (Sec. 3.3 steps 1-2,
+// Plan construction of libaahrt: stretched-time sampling (Sec. 3.4 steps 1-2,
 // eq. q3), azimuth binning of the traces (theta factors of eq. thli),
-// resampler tables of the stretch S and its undoing U (Sec. 3.3: a local
+// resampler tables of the stretch S and its undoing U (Sec. 3.4: a local
 // "spline" interpolation; here Keys' cubic convolution or linear), the
 // spreading kernel of the q-slice, device workspace and work lists.
 #include <algorithm>

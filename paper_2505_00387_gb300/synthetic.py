@@ -7,7 +7,7 @@ time stretch, no Fourier slice, no azimuth binning); both the CUDA path and the
 CPU checker consume the arrays it returns, so either side can be fed the same
 seeded input.
 
-The paper's own synthetic CMP (Sec. 4.1: dt = 4 ms, hyperbolic events with
+The paper's own synthetic CMP (Sec. 5.1: dt = 4 ms, hyperbolic events with
 anisotropic velocities) exists only as a figure, so these generators stand in
 for it with the same sampling and event structure.
 
