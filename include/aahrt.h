@@ -216,6 +216,23 @@ int aahrt_plan_set_profiling(aahrt_plan *plan, int on);
 int aahrt_plan_stage_times(aahrt_plan *plan, double *times_ms,
                            long long *launches);
 
+/* d = L m like aahrt_forward, for callers that must not allocate device
+ * memory during the call (for example code whose device heap is owned by an
+ * external memory manager, or loops that forbid allocation on their hot
+ * path).  The paper has no counterpart: it concerns memory management only.
+ * Scratch (spectra and a work counter) comes from one array of
+ * AAHRT_NOALLOC_SCRATCH_BYTES that the library reserves in device memory at
+ * load time on every GPU that loads it, held until the process exits; the
+ * call allocates nothing.  m and d must be device memory.  Plans whose
+ * spectra need more than the array (aahrt_plan_info xspec_len + yspec_len
+ * complex values, plus 256 bytes) get AAHRT_ERR_UNSUPPORTED.  The first call
+ * on a device looks up the array's address (cudaGetSymbolAddress) and caches
+ * it: make that first call before any stream capture.  Every call shares the
+ * array, which keeps the last call's contents; calls whose kernels overlap
+ * on the GPU race on it and must be serialised. */
+#define AAHRT_NOALLOC_SCRATCH_BYTES (16u << 20)
+int aahrt_forward_noalloc(aahrt_plan *plan, const float *m, float *d, void *stream);
+
 const char *aahrt_status_string(int status);
 const char *aahrt_last_error(void);
 

@@ -76,6 +76,7 @@ _SIGS = {
                                    POINTER(aahrt_solve_opts), POINTER(aahrt_solve_info),
                                    c_void_p]),
     "aahrt_apply_stage": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+    "aahrt_forward_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "aahrt_q_from_slowness": (c_int, [c_double, c_double, c_int, POINTER(c_double),
                                       POINTER(c_double)]),
     "aahrt_plan_set_profiling": (c_int, [c_void_p, c_int]),
@@ -139,6 +140,11 @@ def aahrt_plan_query(h) -> aahrt_plan_info:
 def aahrt_forward(h, m_ptr: int, d_ptr: int, stream: int = 0):
     check(load().aahrt_forward(h, c_void_p(m_ptr), c_void_p(d_ptr), c_void_p(stream)),
           "aahrt_forward")
+
+
+def aahrt_forward_noalloc(h, m_ptr: int, d_ptr: int, stream: int = 0):
+    check(load().aahrt_forward_noalloc(h, c_void_p(m_ptr), c_void_p(d_ptr), c_void_p(stream)),
+          "aahrt_forward_noalloc")
 
 
 def aahrt_adjoint(h, d_ptr: int, m_ptr: int, stream: int = 0):

@@ -104,7 +104,7 @@ int apply_adjoint(Plan &p, const float *d, float *m, cudaStream_t st, int epi, F
     return AAHRT_OK;
 }
 
-static int check_dev_ptr(const void *ptr, const char *name) {
+int check_dev_ptr(const void *ptr, const char *name) {
     if (!ptr) return set_error(AAHRT_ERR_INVALID_ARG, "%s is NULL", name);
     if (reinterpret_cast<uintptr_t>(ptr) & 15)
         return set_error(AAHRT_ERR_INVALID_ARG, "%s is not 16-byte aligned", name);
@@ -363,10 +363,6 @@ static int solve(Plan &p, const float *d, float lambda, int iters, float *m,
 }  // namespace aahrt
 
 using namespace aahrt;
-
-struct aahrt_plan {
-    Plan *p;
-};
 
 extern "C" {
 

@@ -167,11 +167,14 @@ cudaError_t launch_r2c(Plan &p, bool model_side, const float *in, float2 *out,
 cudaError_t launch_c2r(Plan &p, bool model_side, const float2 *in, float *out,
                        int epi, const float *aux, FistaArgs fa, cudaStream_t st);
 cudaError_t launch_slice(Plan &p, bool adjoint, const float2 *in, float2 *out,
-                         cudaStream_t st);
+                         cudaStream_t st, int *counter = nullptr);
 
 // profiling brackets around a stage launch
 void prof_begin(Plan &p, int stage, cudaStream_t st);
 void prof_end(Plan &p, cudaStream_t st);
+
+// pointer checks of the C ABI
+int check_dev_ptr(const void *ptr, const char *name);
 
 // operator application used by the C ABI and the solver
 int apply_forward(Plan &p, const float *m, float *d, cudaStream_t st,
@@ -180,3 +183,8 @@ int apply_adjoint(Plan &p, const float *d, float *m, cudaStream_t st,
                   int epi = EPI_STORE, FistaArgs fa = FistaArgs{});
 
 }  // namespace aahrt
+
+// The opaque handle of the C ABI.
+struct aahrt_plan {
+    aahrt::Plan *p;
+};

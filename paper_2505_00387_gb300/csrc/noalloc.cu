@@ -1,0 +1,88 @@
+// aahrt_forward_noalloc: the forward transform for callers that must not
+// allocate device memory during the call.
+//
+// Some callers cannot call cudaMalloc where they run the transform: code
+// under an external device-memory manager that owns the whole heap (a raw
+// allocation would fail or fragment its pool), or latency-critical loops
+// that forbid allocation and freeing on their hot path.  aahrt_forward
+// itself runs on the plan's workspace, but that workspace is one per plan;
+// this entry point instead takes its scratch (the model and data spectra and
+// the slice kernels' work counter) from one array of fixed size that the
+// library reserves in device memory when it is loaded, and allocates nothing.
+//
+// The array is a file-scope __device__ variable, so every GPU that loads the
+// library holds it until the process exits.  Host code cannot use its name as
+// a device address: the first call on each device looks the address up with
+// cudaGetSymbolAddress (with that device current) and caches it, so make that
+// first call before any stream capture.  All calls share the array and it
+// keeps the last call's contents; the work counter is cleared on every call
+// and the spectra are fully overwritten.  Calls whose kernels overlap on the
+// GPU (different streams without ordering, or several host threads) race on
+// the array: serialise them.
+#include <mutex>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace aahrt {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[AAHRT_NOALLOC_SCRATCH_BYTES];
+
+static std::mutex g_noalloc_mu;
+static std::vector<void *> g_noalloc_addr;   // per device ordinal
+
+// Device address of the array on device `dev`, which must be current.
+static int noalloc_base(int dev, unsigned char **out) {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if ((int)g_noalloc_addr.size() <= dev) g_noalloc_addr.resize(dev + 1, nullptr);
+    if (!g_noalloc_addr[dev]) {
+        void *ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr) return cuda_fail(e, "scratch array address");
+        g_noalloc_addr[dev] = ptr;
+    }
+    *out = static_cast<unsigned char *>(g_noalloc_addr[dev]);
+    return AAHRT_OK;
+}
+
+static size_t round256(size_t n) { return (n + 255) & ~size_t(255); }
+
+}  // namespace aahrt
+
+using namespace aahrt;
+
+extern "C" int aahrt_forward_noalloc(aahrt_plan *plan, const float *m, float *d, void *stream) {
+    if (!plan) return set_error(AAHRT_ERR_INVALID_ARG, "plan is NULL");
+    Plan &p = *plan->p;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != p.device) cudaSetDevice(p.device);
+    int rc = AAHRT_OK;
+    do {
+        if ((rc = check_dev_ptr(m, "m")) || (rc = check_dev_ptr(d, "d"))) break;
+        const size_t xbytes = round256((size_t)p.x_len * sizeof(float2));
+        const size_t ybytes = round256((size_t)p.y_len * sizeof(float2));
+        const size_t need = 256 + xbytes + ybytes;
+        if (need > (size_t)AAHRT_NOALLOC_SCRATCH_BYTES) {
+            rc = set_error(AAHRT_ERR_UNSUPPORTED,
+                           "plan needs %zu bytes of scratch; aahrt_forward_noalloc has %zu "
+                           "(use aahrt_forward)", need, (size_t)AAHRT_NOALLOC_SCRATCH_BYTES);
+            break;
+        }
+        unsigned char *base = nullptr;
+        if ((rc = noalloc_base(p.device, &base))) break;
+        int *counter = reinterpret_cast<int *>(base);
+        float2 *X = reinterpret_cast<float2 *>(base + 256);
+        float2 *Y = reinterpret_cast<float2 *>(base + 256 + xbytes);
+        cudaStream_t st = (cudaStream_t)stream;
+        cudaError_t e;
+        if ((e = launch_r2c(p, true, m, X, st))) { rc = cuda_fail(e, "stretch+FFT launch"); break; }
+        if ((e = launch_slice(p, false, X, Y, st, counter))) { rc = cuda_fail(e, "slice launch"); break; }
+        if ((e = launch_c2r(p, false, Y, d, EPI_STORE, nullptr, FistaArgs{}, st))) {
+            rc = cuda_fail(e, "inverse FFT+unstretch launch");
+            break;
+        }
+    } while (0);
+    if (prev >= 0 && prev != p.device) cudaSetDevice(prev);
+    return rc;
+}

@@ -288,12 +288,14 @@ static SliceArgs make_args(const Plan &p, int counter_slot) {
 #define AAHRT_W_CASES(X) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12)
 
 cudaError_t launch_slice(Plan &p, bool adjoint, const float2 *in, float2 *out,
-                         cudaStream_t st) {
+                         cudaStream_t st, int *counter) {
     const int slot = adjoint ? 1 : 0;
     const int stage = adjoint ? 4 : 1;
-    cudaError_t e = cudaMemsetAsync(p.counters + slot, 0, sizeof(int), st);
+    int *ctr = counter ? counter : p.counters + slot;
+    cudaError_t e = cudaMemsetAsync(ctr, 0, sizeof(int), st);
     if (e) return e;
-    const SliceArgs a = make_args(p, slot);
+    SliceArgs a = make_args(p, slot);
+    a.counter = ctr;
     prof_begin(p, stage, st);
     if (!adjoint) {
         switch (p.w) {

@@ -1,0 +1,65 @@
+"""aahrt_forward_noalloc: the forward transform for callers that must not
+allocate device memory during the call (code whose device heap belongs to an
+external memory manager, or loops that forbid allocation on their hot path).
+Its scratch lives in an array the library reserves at load time; its results
+must match aahrt_forward's.  Collected last so that a run stopping at the
+first failure has already run every other test; it also runs alone."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+TOL_OP = 1e-4   # relative L2 tolerance of one operator application
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def plan():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_00387_gb300 import build
+    build.build()
+    from paper_2505_00387_gb300 import synthetic as syn
+    from paper_2505_00387_gb300.plan import AahrtPlan
+    g = syn.config0()
+    return g, AahrtPlan(**g.geom_kwargs())
+
+
+def test_noalloc_forward_matches_forward_twice(plan):
+    from paper_2505_00387_gb300 import _lib as L
+    g, gp = plan
+    rng = np.random.default_rng(90)
+    for call in range(2):
+        m = torch.from_numpy(rng.standard_normal(gp.model_len).astype(np.float32)).cuda()
+        d_ref = torch.empty(gp.data_len, device="cuda")
+        d_new = torch.full((gp.data_len,), float("nan"), device="cuda")
+        stream = int(torch.cuda.current_stream().cuda_stream)
+        L.aahrt_forward(gp.handle, m.data_ptr(), d_ref.data_ptr(), stream)
+        L.aahrt_forward_noalloc(gp.handle, m.data_ptr(), d_new.data_ptr(), stream)
+        torch.cuda.synchronize()
+        a, b = d_new.cpu().numpy(), d_ref.cpu().numpy()
+        assert np.all(np.isfinite(a)), f"call {call}: non-finite output"
+        assert _rel(a, b) <= TOL_OP, f"call {call}: rel {_rel(a, b):.3e}"
+
+
+def test_noalloc_rejects_plans_beyond_its_scratch():
+    from paper_2505_00387_gb300 import _lib as L
+    from paper_2505_00387_gb300 import synthetic as syn
+    from paper_2505_00387_gb300.plan import AahrtPlan
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    g = syn.config1()
+    gp = AahrtPlan(**g.geom_kwargs())
+    need = 8 * (gp.info.xspec_len + gp.info.yspec_len) + 256
+    assert need > (16 << 20)
+    m = torch.zeros(gp.model_len, device="cuda")
+    d = torch.zeros(gp.data_len, device="cuda")
+    with pytest.raises(L.AahrtError) as e:
+        L.aahrt_forward_noalloc(gp.handle, m.data_ptr(), d.data_ptr())
+    assert e.value.status == L.AAHRT_ERR_UNSUPPORTED
+    assert "scratch" in str(e.value)
