@@ -86,22 +86,53 @@ static cudaError_t reduce(Plan &p, const float *x, const float *y, long long n, 
 
 // ------------------------------------------------------------ operators
 int apply_forward(Plan &p, const float *m, float *d, cudaStream_t st, int epi,
-                  const float *dobs) {
+                  const float *dobs, bool blocked) {
     cudaError_t e;
-    if ((e = launch_r2c(p, true, m, p.X, st))) return cuda_fail(e, "stretch+FFT launch");
+    if ((e = launch_r2c(p, true, m, p.X, st, blocked))) return cuda_fail(e, "stretch+FFT launch");
     if ((e = launch_slice(p, false, p.X, p.Y, st))) return cuda_fail(e, "slice launch");
-    if ((e = launch_c2r(p, false, p.Y, d, epi, dobs, FistaArgs{}, st)))
+    if ((e = launch_c2r(p, false, p.Y, d, epi, dobs, FistaArgs{}, st, blocked)))
         return cuda_fail(e, "inverse FFT+unstretch launch");
     return AAHRT_OK;
 }
 
-int apply_adjoint(Plan &p, const float *d, float *m, cudaStream_t st, int epi, FistaArgs fa) {
+int apply_adjoint(Plan &p, const float *d, float *m, cudaStream_t st, int epi, FistaArgs fa,
+                  bool blocked) {
     cudaError_t e;
-    if ((e = launch_r2c(p, false, d, p.Y, st))) return cuda_fail(e, "unstretch^T+FFT launch");
+    if ((e = launch_r2c(p, false, d, p.Y, st, blocked)))
+        return cuda_fail(e, "unstretch^T+FFT launch");
     if ((e = launch_slice(p, true, p.Y, p.X, st))) return cuda_fail(e, "slice adjoint launch");
-    if ((e = launch_c2r(p, true, p.X, m, epi, nullptr, fa, st)))
+    if ((e = launch_c2r(p, true, p.X, m, epi, nullptr, fa, st, blocked)))
         return cuda_fail(e, "inverse FFT+stretch^T launch");
     return AAHRT_OK;
+}
+
+// Copy between the row-major layout of the C ABI and the column-blocked
+// layout [group][row][2*pairs] of the solver's internal arrays.
+__global__ void reblock_kernel(const float *__restrict__ src, float *__restrict__ dst,
+                               const ColGroup *__restrict__ nat,
+                               const ColGroup *__restrict__ blk, int nrows, int lcpg,
+                               int to_blocked) {
+    const ColGroup a = nat[blockIdx.x], b = blk[blockIdx.x];
+    const int cpg = 1 << lcpg;
+    for (int idx = threadIdx.x; idx < nrows * cpg; idx += blockDim.x) {
+        const int r = idx >> lcpg, c = idx & (cpg - 1);
+        if (c >= a.ncol) continue;
+        const long long io = a.real_off + (long long)r * a.ld_real + c;
+        const long long ib = b.real_off + (long long)r * cpg + c;
+        if (to_blocked) dst[ib] = src[io];
+        else dst[io] = src[ib];
+    }
+}
+
+static cudaError_t reblock(Plan &p, bool model_side, const float *src, float *dst,
+                           bool to_blocked, cudaStream_t st) {
+    const int n = model_side ? p.ncg_model : p.ncg_data;
+    reblock_kernel<<<n, 256, 0, st>>>(src, dst, model_side ? p.cg_model : p.cg_data,
+                                      model_side ? p.cg_model_blk : p.cg_data_blk,
+                                      model_side ? p.ntau : p.nt, p.lp + 1,
+                                      to_blocked ? 1 : 0);
+    p.launches[6]++;
+    return cudaGetLastError();
 }
 
 int check_dev_ptr(const void *ptr, const char *name) {
@@ -208,6 +239,14 @@ static int ensure_solver_ws(Plan &p) {
         return cuda_fail(e, "alloc solver workspace");
     if (!p.scal && (e = cudaMalloc((void **)&p.scal, SC_COUNT * sizeof(double))))
         return cuda_fail(e, "alloc solver workspace");
+    float **mbufs[2] = {&p.zb, &p.mb};
+    for (float **b : mbufs)
+        if (!*b && (e = cudaMalloc((void **)b, p.mblk_len * sizeof(float))))
+            return cuda_fail(e, "alloc solver workspace");
+    float **dbufs[2] = {&p.rb, &p.db};
+    for (float **b : dbufs)
+        if (!*b && (e = cudaMalloc((void **)b, p.dblk_len * sizeof(float))))
+            return cuda_fail(e, "alloc solver workspace");
     return AAHRT_OK;
 }
 
@@ -218,15 +257,16 @@ static int read_scalars(Plan &p, double *h, cudaStream_t st) {
     return e ? cuda_fail(e, "read solver scalars") : AAHRT_OK;
 }
 
-// The iterations proper: per iteration one forward with the residual fused
-// (r = d - L z) and one adjoint with the shrinkage/momentum update fused.
-static int run_iterations(Plan &p, const float *d, float *m, int iters, float gamma,
-                          float thresh, const std::vector<double> &betas, cudaStream_t st) {
+// The iterations proper, on the column-blocked state (mb, zb) and data (db):
+// per iteration one forward with the residual fused (rb = db - L zb) and one
+// adjoint with the shrinkage/momentum update fused.
+static int run_iterations(Plan &p, int iters, float gamma, float thresh,
+                          const std::vector<double> &betas, cudaStream_t st) {
     for (int it = 0; it < iters; ++it) {
-        int rc = apply_forward(p, p.z, p.r, st, EPI_RESIDUAL, d);
+        int rc = apply_forward(p, p.zb, p.rb, st, EPI_RESIDUAL, p.db, true);
         if (rc) return rc;
-        FistaArgs fa{m, p.z, gamma, thresh, (float)betas[it]};
-        rc = apply_adjoint(p, p.r, nullptr, st, EPI_FISTA, fa);
+        FistaArgs fa{p.mb, p.zb, gamma, thresh, (float)betas[it]};
+        rc = apply_adjoint(p, p.rb, nullptr, st, EPI_FISTA, fa, true);
         if (rc) return rc;
     }
     return AAHRT_OK;
@@ -286,10 +326,15 @@ static int solve(Plan &p, const float *d, float lambda, int iters, float *m,
         return set_error(AAHRT_ERR_INVALID_ARG, "gamma (%g) and lambda (%g) must be finite, "
                          "gamma > 0, lambda >= 0", gamma, lam);
 
-    // starting point: m0 (warm) or 0, and z0 = m0
-    if (!o.warm_start && (e = cudaMemsetAsync(m, 0, p.model_len * sizeof(float), st)))
+    // column-blocked copies: data, starting point m0 (warm) or 0, and z0 = m0
+    if ((e = reblock(p, false, d, p.db, true, st))) return cuda_fail(e, "reblock data");
+    if (o.warm_start) {
+        if ((e = reblock(p, true, m, p.mb, true, st))) return cuda_fail(e, "reblock model");
+    } else if ((e = cudaMemsetAsync(p.mb, 0, p.mblk_len * sizeof(float), st))) {
         return cuda_fail(e, "clear model");
-    if ((e = cudaMemcpyAsync(p.z, m, p.model_len * sizeof(float), cudaMemcpyDeviceToDevice, st)))
+    }
+    if ((e = cudaMemcpyAsync(p.zb, p.mb, p.mblk_len * sizeof(float), cudaMemcpyDeviceToDevice,
+                             st)))
         return cuda_fail(e, "copy model");
 
     std::vector<double> betas(std::max(iters, 1), 0.0);
@@ -305,8 +350,7 @@ static int solve(Plan &p, const float *d, float lambda, int iters, float *m,
     if (iters > 0) {
         if (o.use_graph && !p.profiling) {
             char key[256];
-            snprintf(key, sizeof key, "%p/%p/%d/%.9g/%.9g/%d", (const void *)d, (void *)m, iters,
-                     (double)fg, (double)fth, o.ista);
+            snprintf(key, sizeof key, "%d/%.9g/%.9g/%d", iters, (double)fg, (double)fth, o.ista);
             if (!p.gexec || p.gkey != key) {
                 if (p.gexec) { cudaGraphExecDestroy(p.gexec); p.gexec = nullptr; }
                 cudaStream_t cs;
@@ -317,7 +361,7 @@ static int solve(Plan &p, const float *d, float lambda, int iters, float *m,
                 cudaGraph_t graph = nullptr;
                 e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
                 if (!e) {
-                    rc = run_iterations(p, d, m, iters, fg, fth, betas, cs);
+                    rc = run_iterations(p, iters, fg, fth, betas, cs);
                     cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
                     if (!e) e = e2;
                 }
@@ -339,9 +383,11 @@ static int solve(Plan &p, const float *d, float lambda, int iters, float *m,
             // each iteration launches one kernel per operator stage
             for (int s = 0; s < 6; ++s) p.launches[s] += iters;
         } else {
-            if ((rc = run_iterations(p, d, m, iters, fg, fth, betas, st))) return rc;
+            if ((rc = run_iterations(p, iters, fg, fth, betas, st))) return rc;
         }
     }
+
+    if ((e = reblock(p, true, p.mb, m, false, st))) return cuda_fail(e, "reblock model");
 
     if (info) {
         if ((rc = apply_forward(p, m, p.r, st, EPI_RESIDUAL, d))) return rc;

@@ -76,21 +76,22 @@ __host__ __device__ __forceinline__ T ldg_ro(const T *p) {
 #endif
 }
 
-// Complex sequence stored interleaved (float2) with padded indexing.
+// Complex sequence stored interleaved (float2) with padded indexing.  ld/st
+// take a logical index, ldp/stp an already padded one.
 struct IBuf {
     float2 *p;
     __host__ __device__ __forceinline__ float2 ld(int i) const { return p[padi(i)]; }
     __host__ __device__ __forceinline__ void st(int i, float2 v) const { p[padi(i)] = v; }
+    __host__ __device__ __forceinline__ float2 ldp(int j) const { return p[j]; }
+    __host__ __device__ __forceinline__ void stp(int j, float2 v) const { p[j] = v; }
 };
 // Complex sequence stored as separate real and imaginary planes.
 struct SBuf {
     float *re, *im;
-    __host__ __device__ __forceinline__ float2 ld(int i) const {
-        const int j = padi(i);
-        return make_float2(re[j], im[j]);
-    }
-    __host__ __device__ __forceinline__ void st(int i, float2 v) const {
-        const int j = padi(i);
+    __host__ __device__ __forceinline__ float2 ld(int i) const { return ldp(padi(i)); }
+    __host__ __device__ __forceinline__ void st(int i, float2 v) const { stp(padi(i), v); }
+    __host__ __device__ __forceinline__ float2 ldp(int j) const { return make_float2(re[j], im[j]); }
+    __host__ __device__ __forceinline__ void stp(int j, float2 v) const {
         re[j] = v.x;
         im[j] = v.y;
     }
@@ -177,16 +178,22 @@ __host__ __device__ __forceinline__ int rev_bits_c(int m) {
 // radix-2^A DIF network followed by the post-twiddles
 // exp(-2 pi i j rev_A(m) / 2^(lhs+A)) of output m (j = offset of the group).
 // INV = true conjugates every twiddle (inverse transform).
+//
+// The element indices base + (m << lhs) of a group split into disjoint bit
+// fields, so padi(base + (m << lhs)) = padi(base) + padi(m << lhs): the
+// caller passes off[m] = padi(m << lhs), computed once per fused step.
 template <int A, bool INV, class B>
 __host__ __device__ __forceinline__ void dif_group(const B &p, int L, int s, int g,
-                                                   const float2 *__restrict__ tw) {
+                                                   const float2 *__restrict__ tw,
+                                                   const int *off) {
     constexpr int R = 1 << A;
     const int lhs = L - s - A;                 // log2 of the smallest half span
     const int j = g & ((1 << lhs) - 1);
     const int base = ((g >> lhs) << (L - s)) | j;
+    const int pb = padi(base);
     float2 v[R];
 #pragma unroll
-    for (int m = 0; m < R; ++m) v[m] = p.ld(base + (m << lhs));
+    for (int m = 0; m < R; ++m) v[m] = p.ldp(pb + off[m]);
 #pragma unroll
     for (int t = 0; t < A; ++t) {
         const int Mt = R >> (t + 1);
@@ -206,7 +213,7 @@ __host__ __device__ __forceinline__ void dif_group(const B &p, int L, int s, int
         for (int m = 1; m < R; ++m) v[m] = cmul(v[m], w[rev_bits_c<A>(m)]);
     }
 #pragma unroll
-    for (int m = 0; m < R; ++m) p.st(base + (m << lhs), v[m]);
+    for (int m = 0; m < R; ++m) p.stp(pb + off[m], v[m]);
 }
 
 // One radix-2^A DIT group (fused stages s..s+A-1 of the DIT recursion):
@@ -214,13 +221,15 @@ __host__ __device__ __forceinline__ void dif_group(const B &p, int L, int s, int
 // constant radix-2^A DIT network.
 template <int A, bool INV, class B>
 __host__ __device__ __forceinline__ void dit_group(const B &p, int L, int s, int g,
-                                                   const float2 *__restrict__ tw) {
+                                                   const float2 *__restrict__ tw,
+                                                   const int *off) {
     constexpr int R = 1 << A;
     const int low = g & ((1 << s) - 1);
     const int base = ((g >> s) << (s + A)) | low;
+    const int pb = padi(base);
     float2 v[R];
 #pragma unroll
-    for (int m = 0; m < R; ++m) v[m] = p.ld(base + (m << s));
+    for (int m = 0; m < R; ++m) v[m] = p.ldp(pb + off[m]);
     if (low != 0) {
         float2 w[R];
         group_twiddles<A, INV>(low, L, s + A, tw, w);
@@ -240,7 +249,7 @@ __host__ __device__ __forceinline__ void dit_group(const B &p, int L, int s, int
         }
     }
 #pragma unroll
-    for (int m = 0; m < R; ++m) p.st(base + (m << s), v[m]);
+    for (int m = 0; m < R; ++m) p.stp(pb + off[m], v[m]);
 }
 
 // Fused-step schedule: steps of 4 radix-2 stages, the remainder last.
@@ -249,53 +258,70 @@ __host__ __device__ __forceinline__ int fused_width(int L, int s) {
     return r >= 4 ? 4 : r;
 }
 
-template <bool DIF, bool INV, class Batch>
-__host__ __device__ __forceinline__ void fft_group(const Batch &bt, int L, int s, int A, int w,
-                                                   const float2 *__restrict__ tw) {
-    const auto p = bt(w >> (L - A));
-    const int g = w & ((1 << (L - A)) - 1);
-    if (DIF) {
+// off[m] = padi(m << sh) for m < 2^A: the padded offsets of a group's
+// elements from its base (sh = lhs for DIF, s for DIT).
+template <int A>
+__host__ __device__ __forceinline__ void group_offsets(int sh, int *off) {
+#pragma unroll
+    for (int m = 0; m < (1 << A); ++m) off[m] = padi(m << sh);
+}
+
+template <bool DIF, bool INV, int A, class Batch>
+__host__ __device__ __forceinline__ void fft_step(const Batch &bt, int nb, int L, int s,
+                                                  int w0, int dw,
+                                                  const float2 *__restrict__ tw) {
+    int off[1 << A];
+    group_offsets<A>(DIF ? L - s - A : s, off);
+    const int total = nb << (L - A);
+    for (int w = w0; w < total; w += dw) {
+        const auto p = bt(w >> (L - A));
+        const int g = w & ((1 << (L - A)) - 1);
+        if (DIF)
+            dif_group<A, INV>(p, L, s, g, tw, off);
+        else
+            dit_group<A, INV>(p, L, s, g, tw, off);
+    }
+}
+
+// All fused steps of nb sequences of length 2^L, groups w = w0, w0 + dw, ...
+// of each step (one thread's share); the caller synchronises between steps
+// through `sync`.
+template <bool DIF, bool INV, class Batch, class Sync>
+__host__ __device__ __forceinline__ void fft_steps(const Batch &bt, int nb, int L, int w0,
+                                                   int dw, const float2 *__restrict__ tw,
+                                                   Sync sync) {
+    for (int s = 0; s < L;) {
+        const int A = fused_width(L, s);
         switch (A) {
-            case 4: dif_group<4, INV>(p, L, s, g, tw); break;
-            case 3: dif_group<3, INV>(p, L, s, g, tw); break;
-            case 2: dif_group<2, INV>(p, L, s, g, tw); break;
-            default: dif_group<1, INV>(p, L, s, g, tw); break;
+            case 4: fft_step<DIF, INV, 4>(bt, nb, L, s, w0, dw, tw); break;
+            case 3: fft_step<DIF, INV, 3>(bt, nb, L, s, w0, dw, tw); break;
+            case 2: fft_step<DIF, INV, 2>(bt, nb, L, s, w0, dw, tw); break;
+            default: fft_step<DIF, INV, 1>(bt, nb, L, s, w0, dw, tw); break;
         }
-    } else {
-        switch (A) {
-            case 4: dit_group<4, INV>(p, L, s, g, tw); break;
-            case 3: dit_group<3, INV>(p, L, s, g, tw); break;
-            case 2: dit_group<2, INV>(p, L, s, g, tw); break;
-            default: dit_group<1, INV>(p, L, s, g, tw); break;
-        }
+        s += A;
+        sync();
     }
 }
 
 #ifdef __CUDACC__
+struct BlockSync {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
 // nb sequences of length 2^L (bt(b) gives sequence b).  Must be called by
 // every thread of the block; ends with a __syncthreads.
 template <bool DIF, bool INV, class Batch>
 __device__ void block_fft(const Batch &bt, int nb, int L, const float2 *__restrict__ tw) {
-    for (int s = 0; s < L;) {
-        const int A = fused_width(L, s);
-        const int total = nb << (L - A);
-        for (int w = threadIdx.x; w < total; w += blockDim.x)
-            fft_group<DIF, INV>(bt, L, s, A, w, tw);
-        s += A;
-        __syncthreads();
-    }
+    fft_steps<DIF, INV>(bt, nb, L, (int)threadIdx.x, (int)blockDim.x, tw, BlockSync{});
 }
 #endif
 
+struct NoSync {
+    __host__ __device__ void operator()() const {}
+};
 // Host driver of the same groups (used by the CPU test harness).
 template <bool DIF, bool INV, class Batch>
 inline void host_fft(const Batch &bt, int nb, int L, const float2 *tw) {
-    for (int s = 0; s < L;) {
-        const int A = fused_width(L, s);
-        const int total = nb << (L - A);
-        for (int w = 0; w < total; ++w) fft_group<DIF, INV>(bt, L, s, A, w, tw);
-        s += A;
-    }
+    fft_steps<DIF, INV>(bt, nb, L, 0, 1, tw, NoSync{});
 }
 
 }  // namespace aahrt

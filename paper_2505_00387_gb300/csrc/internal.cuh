@@ -115,7 +115,11 @@ struct Plan {
     long long slice_items = 0;
     int *counters = nullptr;       // work counters of the persistent kernels
     ColGroup *cg_model = nullptr, *cg_data = nullptr;
+    // the same column groups over column-blocked arrays [group][row][2*pairs]
+    // (the solver's internal state), every group's rows one contiguous slab
+    ColGroup *cg_model_blk = nullptr, *cg_data_blk = nullptr;
     int ncg_model = 0, ncg_data = 0;
+    long long mblk_len = 0, dblk_len = 0;
     RowPos *posS = nullptr, *posU = nullptr;       // resampler tables
     RowRange *rngST = nullptr, *rngUT = nullptr;
     DevResampler S{}, ST{}, U{}, UT{};
@@ -130,6 +134,7 @@ struct Plan {
     long long x_len = 0, y_len = 0;
     // solver workspace (allocated on first solve)
     float *z = nullptr, *r = nullptr, *v = nullptr;
+    float *zb = nullptr, *mb = nullptr, *rb = nullptr, *db = nullptr;   // column-blocked
     double *scal = nullptr;        // device scalars of the solver
     float *stage_m = nullptr, *stage_d = nullptr;   // staging of host buffers
     // cached graph of the last solve
@@ -163,9 +168,10 @@ int cuda_fail(cudaError_t e, const char *what);
 
 // stage launchers (stream-ordered, no synchronisation)
 cudaError_t launch_r2c(Plan &p, bool model_side, const float *in, float2 *out,
-                       cudaStream_t st);
+                       cudaStream_t st, bool blocked = false);
 cudaError_t launch_c2r(Plan &p, bool model_side, const float2 *in, float *out,
-                       int epi, const float *aux, FistaArgs fa, cudaStream_t st);
+                       int epi, const float *aux, FistaArgs fa, cudaStream_t st,
+                       bool blocked = false);
 cudaError_t launch_slice(Plan &p, bool adjoint, const float2 *in, float2 *out,
                          cudaStream_t st, int *counter = nullptr);
 
@@ -178,9 +184,9 @@ int check_dev_ptr(const void *ptr, const char *name);
 
 // operator application used by the C ABI and the solver
 int apply_forward(Plan &p, const float *m, float *d, cudaStream_t st,
-                  int epi = EPI_STORE, const float *dobs = nullptr);
+                  int epi = EPI_STORE, const float *dobs = nullptr, bool blocked = false);
 int apply_adjoint(Plan &p, const float *d, float *m, cudaStream_t st,
-                  int epi = EPI_STORE, FistaArgs fa = FistaArgs{});
+                  int epi = EPI_STORE, FistaArgs fa = FistaArgs{}, bool blocked = false);
 
 }  // namespace aahrt
 

@@ -180,8 +180,9 @@ void free_plan(Plan *p) {
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
     void *ptrs[] = {p->tw_t, p->tw_q, p->dec, p->geo, p->groups, p->slice_start, p->counters,
-                    p->cg_model, p->cg_data, p->posS, p->posU, p->rngST, p->rngUT, p->X, p->Y,
-                    p->z, p->r, p->v, p->scal, p->stage_m, p->stage_d};
+                    p->cg_model, p->cg_data, p->cg_model_blk, p->cg_data_blk, p->posS,
+                    p->posU, p->rngST, p->rngUT, p->X, p->Y, p->z, p->r, p->v, p->scal,
+                    p->stage_m, p->stage_d, p->zb, p->mb, p->rb, p->db};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     cudaSetDevice(cur);
@@ -233,8 +234,8 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
     }
     if (opts.interp_kind != AAHRT_INTERP_KEYS && opts.interp_kind != AAHRT_INTERP_LINEAR)
         return set_error(AAHRT_ERR_INVALID_ARG, "interp_kind must be 0 or 1");
-    const int W = opts.spread_width ? opts.spread_width : 7;
-    if (W < kMinW || W > kMaxW)
+    int W = opts.spread_width;
+    if (W != 0 && (W < kMinW || W > kMaxW))
         return set_error(AAHRT_ERR_INVALID_ARG, "spread_width must be in [%d, %d]", kMinW, kMaxW);
     if (opts.sigma_t < 0.0 || (opts.sigma_t > 0.0 && opts.sigma_t < 1.0))
         return set_error(AAHRT_ERR_INVALID_ARG, "sigma_t must be 0 (default) or >= 1");
@@ -251,7 +252,6 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
     p->dq = g0.nq > 1 ? g0.dq : 0.0;
     p->ntheta = g0.ntheta;
     p->interp = opts.interp_kind;
-    p->w = W;
     p->sigma_t = opts.sigma_t > 0.0 ? opts.sigma_t : 2.0;
     p->fmax = opts.fmax;
     p->ncube = ncube;
@@ -294,6 +294,13 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
     p->Lq = ilog2(p->nos);
     p->cq = p->nq / 2;
     const double sigma_q = (double)p->nos / p->nq;
+    if (W == 0) {
+        // smallest width whose spreading error exp(-pi W sqrt(1 - 1/sigma))
+        // is below 1e-6 (about 2e-6 measured for sigma = 2..2.6)
+        W = (int)std::ceil(-std::log(1e-6) / (M_PI * std::sqrt(1.0 - 1.0 / sigma_q)));
+        W = std::max(kMinW + 1, std::min(kMaxW, W));
+    }
+    p->w = W;
     p->beta = 0.97 * M_PI * W * (1.0 - 1.0 / (2.0 * sigma_q));
     std::vector<float> dec(p->nq);
     for (int l = 0; l < p->nq; ++l)
@@ -407,6 +414,17 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
         }
     p->ncg_model = (int)cgm.size();
     p->ncg_data = (int)cgd.size();
+    std::vector<ColGroup> cgmb = cgm, cgdb = cgd;
+    for (size_t gi = 0; gi < cgmb.size(); ++gi) {
+        cgmb[gi].real_off = (long long)gi * p->ntau * cpg;
+        cgmb[gi].ld_real = cpg;
+    }
+    for (size_t gi = 0; gi < cgdb.size(); ++gi) {
+        cgdb[gi].real_off = (long long)gi * p->nt * cpg;
+        cgdb[gi].ld_real = cpg;
+    }
+    p->mblk_len = (long long)p->ncg_model * p->ntau * cpg;
+    p->dblk_len = (long long)p->ncg_data * p->nt * cpg;
 
     // ------------------------------------------------------ resamplers
     std::vector<double> upos(p->ns), vpos(p->nt);
@@ -468,6 +486,8 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
     AAHRT_TRY(upload(&p->slice_start, ss_all), "upload slice table");
     AAHRT_TRY(upload(&p->cg_model, cgm), "upload column groups");
     AAHRT_TRY(upload(&p->cg_data, cgd), "upload column groups");
+    AAHRT_TRY(upload(&p->cg_model_blk, cgmb), "upload column groups");
+    AAHRT_TRY(upload(&p->cg_data_blk, cgdb), "upload column groups");
     AAHRT_TRY(upload(&p->posS, posS), "upload resamplers");
     AAHRT_TRY(upload(&p->posU, posU), "upload resamplers");
     AAHRT_TRY(upload(&p->rngST, rngST), "upload resamplers");

@@ -170,7 +170,7 @@ slice_adj_kernel(const SliceArgs a, const float2 *__restrict__ Y, float2 *__rest
     float *smf = reinterpret_cast<float *>(smem_f4);
     __shared__ long long s_item;
     __shared__ float s_sa[kMaxGroupSlices + 1], s_sb[kMaxGroupSlices + 1];
-    __shared__ float s_fx[kMaxGroupSlices];
+    __shared__ float s_fx[kMaxGroupSlices], s_ifx[kMaxGroupSlices];
     const int lds = ld_split(a.nos);
     const int mask = a.nos - 1;
     for (;;) {
@@ -230,6 +230,7 @@ slice_adj_kernel(const SliceArgs a, const float2 *__restrict__ Y, float2 *__rest
             const float prev = jj > 0 ? s_sb[jj - 1] : (a.ngroup > 1 ? s_sb[g.nj] : s_sb[g.nj - 1]);
             const float bound = (s_sa[jj] + prev) * a.scale * a.phimax;
             s_fx[jj] = bound > 0.f ? 1073741824.0f / bound : 0.f;   // 2^30 / bound
+            s_ifx[jj] = bound > 0.f ? bound * 9.3132257461547852e-10f : 0.f;   // 1/fx
         }
         __syncthreads();
 
@@ -239,12 +240,11 @@ slice_adj_kernel(const SliceArgs a, const float2 *__restrict__ Y, float2 *__rest
             spread_trace<W>(a, g, geo[t], Yk, k, Ire, Iim, lds, mask, s_fx);
         __syncthreads();
         // back to floating point, in place (slice jj sits in rows jj and nj + jj)
-        const float inv_lds = 1.0f / (float)lds;
-        for (int idx = threadIdx.x; idx < 2 * g.nj * lds; idx += blockDim.x) {
-            int jj = fast_div(idx, lds, inv_lds);
-            if (jj >= g.nj) jj -= g.nj;
-            const float f = s_fx[jj];
-            smf[idx] = f > 0.f ? (float)reinterpret_cast<int *>(smf)[idx] / f : 0.f;
+        for (int row = threadIdx.x >> 5; row < 2 * g.nj; row += kThreadsSlice / 32) {
+            const float f = s_ifx[row < g.nj ? row : row - g.nj];
+            float *rp = smf + row * lds;
+            for (int u = threadIdx.x & 31; u < lds; u += 32)
+                rp[u] = (float)reinterpret_cast<int *>(rp)[u] * f;
         }
         __syncthreads();
         block_fft<true, true>(SBatch{Gre, Gim, lds}, g.nj, a.Lq, a.tw);

@@ -314,8 +314,9 @@ static void c2r_launch(bool model_side, int grid, size_t smem, cudaStream_t st,
     else { constexpr int IPc = AAHRT_INTERP_KEYS; STMT; }
 
 cudaError_t launch_r2c(Plan &p, bool model_side, const float *in, float2 *out,
-                       cudaStream_t st) {
-    const ColGroup *cg = model_side ? p.cg_model : p.cg_data;
+                       cudaStream_t st, bool blocked) {
+    const ColGroup *cg = model_side ? (blocked ? p.cg_model_blk : p.cg_model)
+                                    : (blocked ? p.cg_data_blk : p.cg_data);
     const int n = model_side ? p.ncg_model : p.ncg_data;
     const DevResampler rs = model_side ? p.S : p.UT;
     const int nrow_in = model_side ? p.ntau : p.nt;
@@ -330,8 +331,9 @@ cudaError_t launch_r2c(Plan &p, bool model_side, const float *in, float2 *out,
 }
 
 cudaError_t launch_c2r(Plan &p, bool model_side, const float2 *in, float *out,
-                       int epi, const float *aux, FistaArgs fa, cudaStream_t st) {
-    const ColGroup *cg = model_side ? p.cg_model : p.cg_data;
+                       int epi, const float *aux, FistaArgs fa, cudaStream_t st, bool blocked) {
+    const ColGroup *cg = model_side ? (blocked ? p.cg_model_blk : p.cg_model)
+                                    : (blocked ? p.cg_data_blk : p.cg_data);
     const int n = model_side ? p.ncg_model : p.ncg_data;
     const DevResampler rs = model_side ? p.ST : p.U;
     const int n_in = p.ns;
