@@ -173,6 +173,54 @@ __host__ __device__ __forceinline__ int rev_bits_c(int m) {
     return r;
 }
 
+// Constant radix-2^A DIF network on v[0..2^A) (in place).
+template <int A, bool INV>
+__host__ __device__ __forceinline__ void dif_network(float2 *v) {
+    constexpr int R = 1 << A;
+#pragma unroll
+    for (int t = 0; t < A; ++t) {
+        const int Mt = R >> (t + 1);
+        const int T = A - 1 - t;               // log2 Mt
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+            if (m & Mt) continue;
+            const float2 a = v[m], c = v[m + Mt];
+            v[m] = cadd(a, c);
+            v[m + Mt] = kappa_mul<INV>(csub(a, c), T, m & (Mt - 1));
+        }
+    }
+}
+
+// Constant radix-2^A DIT network on v[0..2^A) (in place).
+template <int A, bool INV>
+__host__ __device__ __forceinline__ void dit_network(float2 *v) {
+    constexpr int R = 1 << A;
+#pragma unroll
+    for (int t = 0; t < A; ++t) {
+        const int Mt = 1 << t;
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+            if (m & Mt) continue;
+            const float2 c = kappa_mul<INV>(v[m + Mt], t, m & (Mt - 1));
+            const float2 a = v[m];
+            v[m] = cadd(a, c);
+            v[m + Mt] = csub(a, c);
+        }
+    }
+}
+
+// v[m] *= exp(-+ 2 pi i q rev_A(m) / 2^X), m >= 1 (nothing when q == 0).
+template <int A, bool INV>
+__host__ __device__ __forceinline__ void group_twiddle(float2 *v, int q, int L, int X,
+                                                       const float2 *__restrict__ tw) {
+    if (q == 0) return;
+    constexpr int R = 1 << A;
+    float2 w[R];
+    group_twiddles<A, INV>(q, L, X, tw, w);
+#pragma unroll
+    for (int m = 1; m < R; ++m) v[m] = cmul(v[m], w[rev_bits_c<A>(m)]);
+}
+
 // One radix-2^A DIF group: fused stages s..s+A-1 of the DIF recursion for a
 // sequence of N = 2^L, group index g < N >> A.  Written as the constant
 // radix-2^A DIF network followed by the post-twiddles
@@ -189,29 +237,12 @@ __host__ __device__ __forceinline__ void dif_group(const B &p, int L, int s, int
     constexpr int R = 1 << A;
     const int lhs = L - s - A;                 // log2 of the smallest half span
     const int j = g & ((1 << lhs) - 1);
-    const int base = ((g >> lhs) << (L - s)) | j;
-    const int pb = padi(base);
+    const int pb = padi(((g >> lhs) << (L - s)) | j);
     float2 v[R];
 #pragma unroll
     for (int m = 0; m < R; ++m) v[m] = p.ldp(pb + off[m]);
-#pragma unroll
-    for (int t = 0; t < A; ++t) {
-        const int Mt = R >> (t + 1);
-        const int T = A - 1 - t;               // log2 Mt
-#pragma unroll
-        for (int m = 0; m < R; ++m) {
-            if (m & Mt) continue;
-            const float2 a = v[m], c = v[m + Mt];
-            v[m] = cadd(a, c);
-            v[m + Mt] = kappa_mul<INV>(csub(a, c), T, m & (Mt - 1));
-        }
-    }
-    if (j != 0) {
-        float2 w[R];
-        group_twiddles<A, INV>(j, L, lhs + A, tw, w);
-#pragma unroll
-        for (int m = 1; m < R; ++m) v[m] = cmul(v[m], w[rev_bits_c<A>(m)]);
-    }
+    dif_network<A, INV>(v);
+    group_twiddle<A, INV>(v, j, L, lhs + A, tw);
 #pragma unroll
     for (int m = 0; m < R; ++m) p.stp(pb + off[m], v[m]);
 }
@@ -225,29 +256,12 @@ __host__ __device__ __forceinline__ void dit_group(const B &p, int L, int s, int
                                                    const int *off) {
     constexpr int R = 1 << A;
     const int low = g & ((1 << s) - 1);
-    const int base = ((g >> s) << (s + A)) | low;
-    const int pb = padi(base);
+    const int pb = padi(((g >> s) << (s + A)) | low);
     float2 v[R];
 #pragma unroll
     for (int m = 0; m < R; ++m) v[m] = p.ldp(pb + off[m]);
-    if (low != 0) {
-        float2 w[R];
-        group_twiddles<A, INV>(low, L, s + A, tw, w);
-#pragma unroll
-        for (int m = 1; m < R; ++m) v[m] = cmul(v[m], w[rev_bits_c<A>(m)]);
-    }
-#pragma unroll
-    for (int t = 0; t < A; ++t) {
-        const int Mt = 1 << t;
-#pragma unroll
-        for (int m = 0; m < R; ++m) {
-            if (m & Mt) continue;
-            const float2 c = kappa_mul<INV>(v[m + Mt], t, m & (Mt - 1));
-            const float2 a = v[m];
-            v[m] = cadd(a, c);
-            v[m + Mt] = csub(a, c);
-        }
-    }
+    group_twiddle<A, INV>(v, low, L, s + A, tw);
+    dit_network<A, INV>(v);
 #pragma unroll
     for (int m = 0; m < R; ++m) p.stp(pb + off[m], v[m]);
 }
@@ -283,14 +297,16 @@ __host__ __device__ __forceinline__ void fft_step(const Batch &bt, int nb, int L
     }
 }
 
-// All fused steps of nb sequences of length 2^L, groups w = w0, w0 + dw, ...
+// Fused steps starting at stages s_begin .. s_end-1 (step starts are the
+// multiples of 4) of nb sequences of length 2^L, groups w = w0, w0 + dw, ...
 // of each step (one thread's share); the caller synchronises between steps
 // through `sync`.
 template <bool DIF, bool INV, class Batch, class Sync>
 __host__ __device__ __forceinline__ void fft_steps(const Batch &bt, int nb, int L, int w0,
                                                    int dw, const float2 *__restrict__ tw,
-                                                   Sync sync) {
-    for (int s = 0; s < L;) {
+                                                   Sync sync, int s_begin = 0,
+                                                   int s_end = 1 << 30) {
+    for (int s = s_begin; s < L && s < s_end;) {
         const int A = fused_width(L, s);
         switch (A) {
             case 4: fft_step<DIF, INV, 4>(bt, nb, L, s, w0, dw, tw); break;
@@ -310,8 +326,10 @@ struct BlockSync {
 // nb sequences of length 2^L (bt(b) gives sequence b).  Must be called by
 // every thread of the block; ends with a __syncthreads.
 template <bool DIF, bool INV, class Batch>
-__device__ void block_fft(const Batch &bt, int nb, int L, const float2 *__restrict__ tw) {
-    fft_steps<DIF, INV>(bt, nb, L, (int)threadIdx.x, (int)blockDim.x, tw, BlockSync{});
+__device__ void block_fft(const Batch &bt, int nb, int L, const float2 *__restrict__ tw,
+                          int s_begin = 0, int s_end = 1 << 30) {
+    fft_steps<DIF, INV>(bt, nb, L, (int)threadIdx.x, (int)blockDim.x, tw, BlockSync{},
+                        s_begin, s_end);
 }
 #endif
 

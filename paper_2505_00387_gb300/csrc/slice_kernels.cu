@@ -65,26 +65,42 @@ slice_fwd_kernel(const SliceArgs a, const float2 *__restrict__ X, float2 *__rest
         const SliceGroup g = a.groups[gi];
         const int ncolj = g.nj + extra;
 
-        // deapodised, centred columns into bit-reversed grid positions
-        // (grid point u holds column entry l = (u + cq) mod nos when l < nq)
-        const float2 *Xk = X + g.x_off + (long long)k * a.nq * a.ntheta;
-        const float inv_nc = 1.0f / (float)ncolj;
-        for (int idx = threadIdx.x; idx < ncolj * a.nos; idx += blockDim.x) {
-            const int u = fast_div(idx, ncolj, inv_nc);
-            const int jj = idx - u * ncolj;
-            const int l = (u + a.cq) & mask;
-            float2 v = make_float2(0.f, 0.f);
-            if (l < a.nq) {
+        // First DIT step fused with the column load: element m of group g0
+        // (bit-reversed position 16 g0 + m) is grid point
+        // u = brev(16 g0 + m) = (brev4(m) << (Lq - 4)) | brev(g0), holding the
+        // deapodised column entry l = (u + cq) mod nos when l < nq, else zero.
+        {
+            const float2 *Xk = X + g.x_off + (long long)k * a.nq * a.ntheta;
+            const float inv_nc = 1.0f / (float)ncolj;
+            const int items = (a.nos >> 4) * ncolj;
+            int off0[16];
+            group_offsets<4>(0, off0);
+            for (int w = threadIdx.x; w < items; w += blockDim.x) {
+                const int g0 = fast_div(w, ncolj, inv_nc);
+                const int jj = w - g0 * ncolj;
                 int j = g.ja + jj;
                 if (j >= a.ntheta) j -= a.ntheta;
-                const float2 x = __ldg(Xk + (long long)l * a.ntheta + j);
-                const float dl = __ldg(a.dec + l);
-                v = make_float2(x.x * dl, x.y * dl);
+                const int ug = (int)brev_bits(g0, a.Lq - 4);
+                float2 v[16];
+#pragma unroll
+                for (int m = 0; m < 16; ++m) {
+                    const int u = (rev_bits_c<4>(m) << (a.Lq - 4)) | ug;
+                    const int l = (u + a.cq) & mask;
+                    v[m] = make_float2(0.f, 0.f);
+                    if (l < a.nq) {
+                        const float2 x = __ldg(Xk + (long long)l * a.ntheta + j);
+                        const float dl = __ldg(a.dec + l);
+                        v[m] = make_float2(x.x * dl, x.y * dl);
+                    }
+                }
+                dit_network<4, false>(v);
+                float2 *col = G + jj * ldg + padi(g0 << 4);
+#pragma unroll
+                for (int m = 0; m < 16; ++m) col[off0[m]] = v[m];
             }
-            G[jj * ldg + padi(brev_bits(u, a.Lq))] = v;
         }
         __syncthreads();
-        block_fft<false, false>(IBatch{G, ldg}, ncolj, a.Lq, a.tw);
+        block_fft<false, false>(IBatch{G, ldg}, ncolj, a.Lq, a.tw, 4);
 
         // interpolate every owned trace
         const TraceGeo *geo = a.geo + g.geo_off;
@@ -163,6 +179,73 @@ __device__ __forceinline__ void spread_trace(const SliceArgs &a, const SliceGrou
     }
 }
 
+// First DIF step of the adjoint's inverse q-FFT fused with the conversion of
+// the fixed-point grid: group j of column jj holds elements j + (m << (Lq-4));
+// it reads them as integers, scales them back (1/fx of the column), applies
+// the constant radix-16 network and the post-twiddles, and stores floats in
+// place.
+__device__ __forceinline__ void adj_first_step(const SliceArgs &a, const SliceGroup &g,
+                                               float *smf, int lds, const float *ifx) {
+    const int lhs = a.Lq - 4;
+    const int ng = 1 << lhs;
+    int off[16];
+    group_offsets<4>(lhs, off);
+    float *Gre = smf, *Gim = smf + g.nj * lds;
+    const int *Ire = reinterpret_cast<const int *>(Gre);
+    const int *Iim = reinterpret_cast<const int *>(Gim);
+    for (int w = threadIdx.x; w < ng * g.nj; w += blockDim.x) {
+        const int jj = w >> lhs;
+        const int j = w & (ng - 1);
+        const float f = ifx[jj];
+        const int pb = jj * lds + padi(j);
+        float2 v[16];
+#pragma unroll
+        for (int m = 0; m < 16; ++m)
+            v[m] = make_float2((float)Ire[pb + off[m]] * f, (float)Iim[pb + off[m]] * f);
+        dif_network<4, true>(v);
+        group_twiddle<4, true>(v, j, a.Lq, a.Lq, a.tw);
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+            Gre[pb + off[m]] = v[m].x;
+            Gim[pb + off[m]] = v[m].y;
+        }
+    }
+}
+
+// Last DIF step (radix 2^A, no post-twiddles) fused with the deapodised
+// output: output position p = (gg << A) + m is grid point u = brev(p), i.e.
+// column entry l = (u + cq) mod nos, written when l < nq.
+template <int A>
+__device__ __forceinline__ void adj_last_step(const SliceArgs &a, const SliceGroup &g,
+                                              const float *Gre, const float *Gim, int lds,
+                                              int k, float2 *__restrict__ X) {
+    constexpr int R = 1 << A;
+    const int items = (1 << (a.Lq - A)) * g.nj;
+    const float inv_nj = 1.0f / (float)g.nj;
+    const int mask = a.nos - 1;
+    int off[R];
+    group_offsets<A>(0, off);
+    float2 *Xk = X + g.x_off + (long long)k * a.nq * a.ntheta + g.ja;
+    for (int w = threadIdx.x; w < items; w += blockDim.x) {
+        const int gg = fast_div(w, g.nj, inv_nj);
+        const int jj = w - gg * g.nj;
+        const int base = gg << A;
+        const int pb = jj * lds + padi(base);
+        float2 v[R];
+#pragma unroll
+        for (int m = 0; m < R; ++m) v[m] = make_float2(Gre[pb + off[m]], Gim[pb + off[m]]);
+        dif_network<A, true>(v);
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+            const int l = ((int)brev_bits(base + m, a.Lq) + a.cq) & mask;
+            if (l < a.nq) {
+                const float dl = __ldg(a.dec + l);
+                Xk[(long long)l * a.ntheta + jj] = make_float2(v[m].x * dl, v[m].y * dl);
+            }
+        }
+    }
+}
+
 template <int W>
 __global__ void __launch_bounds__(kThreadsSlice, 2)
 slice_adj_kernel(const SliceArgs a, const float2 *__restrict__ Y, float2 *__restrict__ X) {
@@ -191,7 +274,14 @@ slice_adj_kernel(const SliceArgs a, const float2 *__restrict__ Y, float2 *__rest
         // zero the grid; per owned slice, bound its spread by the sums
         // A_j = sum w0 |y| over traces with j0 = j and B_j = sum w1 |y| over
         // traces with j0 = j (whose second weight lands on slice j + 1)
-        for (int idx = threadIdx.x; idx < 2 * g.nj * lds; idx += blockDim.x) smf[idx] = 0.f;
+        {
+            const int nz4 = (2 * g.nj * lds) >> 2;
+            float4 *z4 = reinterpret_cast<float4 *>(smf);
+            for (int idx = threadIdx.x; idx < nz4; idx += blockDim.x)
+                z4[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int idx = 4 * nz4 + threadIdx.x; idx < 2 * g.nj * lds; idx += blockDim.x)
+                smf[idx] = 0.f;
+        }
         const int *sstart = a.slice_start + g.ss_off;
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         const int nseg = g.nj + 1;            // owned slices, then the slice before ja
@@ -239,25 +329,37 @@ slice_adj_kernel(const SliceArgs a, const float2 *__restrict__ Y, float2 *__rest
         for (int t = g.e0 + threadIdx.x; t < g.e1; t += blockDim.x)
             spread_trace<W>(a, g, geo[t], Yk, k, Ire, Iim, lds, mask, s_fx);
         __syncthreads();
-        // back to floating point, in place (slice jj sits in rows jj and nj + jj)
-        for (int row = threadIdx.x >> 5; row < 2 * g.nj; row += kThreadsSlice / 32) {
-            const float f = s_ifx[row < g.nj ? row : row - g.nj];
-            float *rp = smf + row * lds;
-            for (int u = threadIdx.x & 31; u < lds; u += 32)
-                rp[u] = (float)reinterpret_cast<int *>(rp)[u] * f;
-        }
-        __syncthreads();
-        block_fft<true, true>(SBatch{Gre, Gim, lds}, g.nj, a.Lq, a.tw);
-
-        float2 *Xk = X + g.x_off + (long long)k * a.nq * a.ntheta;
-        const float inv_nj = 1.0f / (float)g.nj;
-        for (int idx = threadIdx.x; idx < g.nj * a.nq; idx += blockDim.x) {
-            const int l = fast_div(idx, g.nj, inv_nj);
-            const int jj = idx - l * g.nj;
-            const int u = padi(brev_bits((l - a.cq) & mask, a.Lq));
-            const float dl = __ldg(a.dec + l);
-            Xk[(long long)l * a.ntheta + g.ja + jj] =
-                make_float2(Gre[jj * lds + u] * dl, Gim[jj * lds + u] * dl);
+        if (a.Lq >= 5) {
+            adj_first_step(a, g, smf, lds, s_ifx);
+            __syncthreads();
+            const int s_last = 4 * ((a.Lq - 1) >> 2);
+            block_fft<true, true>(SBatch{Gre, Gim, lds}, g.nj, a.Lq, a.tw, 4, s_last);
+            switch (a.Lq - s_last) {
+                case 4: adj_last_step<4>(a, g, Gre, Gim, lds, k, X); break;
+                case 3: adj_last_step<3>(a, g, Gre, Gim, lds, k, X); break;
+                case 2: adj_last_step<2>(a, g, Gre, Gim, lds, k, X); break;
+                default: adj_last_step<1>(a, g, Gre, Gim, lds, k, X); break;
+            }
+        } else {
+            // back to floating point, in place (slice jj sits in rows jj and nj + jj)
+            for (int row = threadIdx.x >> 5; row < 2 * g.nj; row += kThreadsSlice / 32) {
+                const float f = s_ifx[row < g.nj ? row : row - g.nj];
+                float *rp = smf + row * lds;
+                for (int u = threadIdx.x & 31; u < lds; u += 32)
+                    rp[u] = (float)reinterpret_cast<int *>(rp)[u] * f;
+            }
+            __syncthreads();
+            block_fft<true, true>(SBatch{Gre, Gim, lds}, g.nj, a.Lq, a.tw);
+            float2 *Xk = X + g.x_off + (long long)k * a.nq * a.ntheta;
+            const float inv_nj = 1.0f / (float)g.nj;
+            for (int idx = threadIdx.x; idx < g.nj * a.nq; idx += blockDim.x) {
+                const int l = fast_div(idx, g.nj, inv_nj);
+                const int jj = idx - l * g.nj;
+                const int u = padi(brev_bits((l - a.cq) & mask, a.Lq));
+                const float dl = __ldg(a.dec + l);
+                Xk[(long long)l * a.ntheta + g.ja + jj] =
+                    make_float2(Gre[jj * lds + u] * dl, Gim[jj * lds + u] * dl);
+            }
         }
         __syncthreads();
     }
