@@ -280,20 +280,57 @@ __host__ __device__ __forceinline__ void group_offsets(int sh, int *off) {
     for (int m = 0; m < (1 << A); ++m) off[m] = padi(m << sh);
 }
 
-template <bool DIF, bool INV, int A, class Batch>
+// Twiddles of a group are exp(-+ 2 pi i q rev_A(m) / 2^X) with q the group
+// index's low bits (q = j for DIF, q = low for DIT); a thread's groups in one
+// step usually share q (whenever its group stride is a multiple of 2^qbits),
+// so the twiddles are built once and reused while q stays the same.
+template <bool DIF, bool INV, int A, bool HOIST, class Batch>
 __host__ __device__ __forceinline__ void fft_step(const Batch &bt, int nb, int L, int s,
                                                   int w0, int dw,
                                                   const float2 *__restrict__ tw) {
-    int off[1 << A];
-    group_offsets<A>(DIF ? L - s - A : s, off);
+    constexpr int R = 1 << A;
+    int off[R];
+    const int sh = DIF ? L - s - A : s;        // log2 of the element stride
+    group_offsets<A>(sh, off);
+    const int qmask = (1 << sh) - 1;           // twiddle index: low sh bits of g
+    const int X = DIF ? L - s : s + A;
     const int total = nb << (L - A);
+    float2 wt[R];
+    int qcur = -1;
     for (int w = w0; w < total; w += dw) {
         const auto p = bt(w >> (L - A));
         const int g = w & ((1 << (L - A)) - 1);
-        if (DIF)
-            dif_group<A, INV>(p, L, s, g, tw, off);
-        else
-            dit_group<A, INV>(p, L, s, g, tw, off);
+        if (!HOIST) {
+            if (DIF)
+                dif_group<A, INV>(p, L, s, g, tw, off);
+            else
+                dit_group<A, INV>(p, L, s, g, tw, off);
+            continue;
+        }
+        const int q = g & qmask;
+        if (!HOIST || q != qcur) {
+            if (q != 0) group_twiddles<A, INV>(q, L, X, tw, wt);
+            qcur = q;
+        }
+        const int pb = DIF ? padi(((g >> sh) << (L - s)) | q) : padi(((g >> s) << (s + A)) | q);
+        float2 v[R];
+#pragma unroll
+        for (int m = 0; m < R; ++m) v[m] = p.ldp(pb + off[m]);
+        if (DIF) {
+            dif_network<A, INV>(v);
+            if (q != 0) {
+#pragma unroll
+                for (int m = 1; m < R; ++m) v[m] = cmul(v[m], wt[rev_bits_c<A>(m)]);
+            }
+        } else {
+            if (q != 0) {
+#pragma unroll
+                for (int m = 1; m < R; ++m) v[m] = cmul(v[m], wt[rev_bits_c<A>(m)]);
+            }
+            dit_network<A, INV>(v);
+        }
+#pragma unroll
+        for (int m = 0; m < R; ++m) p.stp(pb + off[m], v[m]);
     }
 }
 
@@ -301,7 +338,7 @@ __host__ __device__ __forceinline__ void fft_step(const Batch &bt, int nb, int L
 // multiples of 4) of nb sequences of length 2^L, groups w = w0, w0 + dw, ...
 // of each step (one thread's share); the caller synchronises between steps
 // through `sync`.
-template <bool DIF, bool INV, class Batch, class Sync>
+template <bool DIF, bool INV, bool HOIST, class Batch, class Sync>
 __host__ __device__ __forceinline__ void fft_steps(const Batch &bt, int nb, int L, int w0,
                                                    int dw, const float2 *__restrict__ tw,
                                                    Sync sync, int s_begin = 0,
@@ -309,10 +346,10 @@ __host__ __device__ __forceinline__ void fft_steps(const Batch &bt, int nb, int 
     for (int s = s_begin; s < L && s < s_end;) {
         const int A = fused_width(L, s);
         switch (A) {
-            case 4: fft_step<DIF, INV, 4>(bt, nb, L, s, w0, dw, tw); break;
-            case 3: fft_step<DIF, INV, 3>(bt, nb, L, s, w0, dw, tw); break;
-            case 2: fft_step<DIF, INV, 2>(bt, nb, L, s, w0, dw, tw); break;
-            default: fft_step<DIF, INV, 1>(bt, nb, L, s, w0, dw, tw); break;
+            case 4: fft_step<DIF, INV, 4, HOIST>(bt, nb, L, s, w0, dw, tw); break;
+            case 3: fft_step<DIF, INV, 3, HOIST>(bt, nb, L, s, w0, dw, tw); break;
+            case 2: fft_step<DIF, INV, 2, HOIST>(bt, nb, L, s, w0, dw, tw); break;
+            default: fft_step<DIF, INV, 1, HOIST>(bt, nb, L, s, w0, dw, tw); break;
         }
         s += A;
         sync();
@@ -325,11 +362,13 @@ struct BlockSync {
 };
 // nb sequences of length 2^L (bt(b) gives sequence b).  Must be called by
 // every thread of the block; ends with a __syncthreads.
-template <bool DIF, bool INV, class Batch>
+// HOIST = true keeps a group's twiddles in registers across the thread's
+// groups with the same twiddle index (more live registers).
+template <bool DIF, bool INV, class Batch, bool HOIST = false>
 __device__ void block_fft(const Batch &bt, int nb, int L, const float2 *__restrict__ tw,
                           int s_begin = 0, int s_end = 1 << 30) {
-    fft_steps<DIF, INV>(bt, nb, L, (int)threadIdx.x, (int)blockDim.x, tw, BlockSync{},
-                        s_begin, s_end);
+    fft_steps<DIF, INV, HOIST>(bt, nb, L, (int)threadIdx.x, (int)blockDim.x, tw, BlockSync{},
+                               s_begin, s_end);
 }
 #endif
 
@@ -339,7 +378,7 @@ struct NoSync {
 // Host driver of the same groups (used by the CPU test harness).
 template <bool DIF, bool INV, class Batch>
 inline void host_fft(const Batch &bt, int nb, int L, const float2 *tw) {
-    fft_steps<DIF, INV>(bt, nb, L, 0, 1, tw, NoSync{});
+    fft_steps<DIF, INV, true>(bt, nb, L, 0, 1, tw, NoSync{});
 }
 
 }  // namespace aahrt

@@ -142,7 +142,7 @@ r2c_kernel(const float *__restrict__ in, float2 *__restrict__ out,
         for (int p = 0; p < P; ++p) sm[p * ld + padi(n)] = acc.v[p];
     }
     __syncthreads();
-    block_fft<true, false>(IBatch{sm, ld}, P, L, tw);
+    block_fft<true, false, IBatch, true>(IBatch{sm, ld}, P, L, tw);
 
     // unpack the two real spectra: A = (Z_k + conj Z_{N-k})/2, B = (Z_k - conj Z_{N-k})/(2i)
     float2 *dst = out + cg.spec_off;
@@ -210,7 +210,7 @@ c2r_kernel(const float2 *__restrict__ in, float *__restrict__ out,
         }
     }
     __syncthreads();
-    block_fft<false, true>(IBatch{sm, ld}, P, L, tw);
+    block_fft<false, true, IBatch, true>(IBatch{sm, ld}, P, L, tw);
 
     // resample the synthesized columns onto the output rows, one row per thread
     for (int i = threadIdx.x; i < rs.nrows; i += blockDim.x) {
