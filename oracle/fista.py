@@ -84,3 +84,54 @@ def solve(plan, d, lam, iters, gamma, momentum: bool = True, m0=None,
         if history:
             hist.append(objective(plan, d, m, lam, impl))
     return (m, hist) if history else m
+
+
+def unrolled_states(plan, d, lam, gamma, iters, momentum: bool = True, impl: str = "c"):
+    """The iterations of `solve` from m^0 = z^0 = 0 with every intermediate
+    kept: lists z[k] (k <= iters), m[k] (k <= iters) and the pre-shrinkage
+    points u[k] = z^k + gamma L^T (d - L z^k) (k < iters), and the
+    extrapolation weights beta_k (zeros for ISTA)."""
+    d = np.asarray(d, np.float64)
+    shape = (plan.ntau, plan.nq, plan.ntheta)
+    betas = momentum_schedule(iters) if momentum else np.zeros(iters)
+    m = [np.zeros(shape)]
+    z = [np.zeros(shape)]
+    u = []
+    for k in range(iters):
+        g = ops.adjoint(plan, d - ops.forward(plan, z[k], impl), impl)
+        u.append(z[k] + gamma * g)
+        m.append(soft(u[k], gamma * lam))
+        z.append(m[k + 1] + betas[k] * (m[k + 1] - m[k]))
+    return z, m, u, betas
+
+
+def unrolled_vjp(plan, d, m_bar, lam, gamma, iters, momentum: bool = True,
+                 impl: str = "c"):
+    """Reverse-mode derivative of the unrolled solve d -> m^iters (fixed
+    gamma and lambda, start 0): returns (m^iters, d_bar) with
+    d_bar = (d m^iters / d d)^T m_bar.
+
+    Each iteration is u = z + gamma L^T (d - L z), m+ = soft(u, t),
+    z+ = (1 + beta) m+ - beta m, with t = gamma*lambda.  Going backwards with
+    the cotangents a_m of m+ and a_z of z+:
+        total cotangent of m+     c = a_m + (1 + beta) a_z
+        through the shrinkage     u_bar = c * [|u| > t]
+        data                      d_bar += gamma L u_bar
+        the iterate z             z_bar = u_bar - gamma L^T L u_bar
+        the previous m            m_bar_prev = -beta a_z
+    The shrinkage has slope 1 where |u| > t and 0 where |u| < t; at |u| = t
+    it has no derivative and the slope 0 is taken."""
+    z, m, u, betas = unrolled_states(plan, d, lam, gamma, iters, momentum, impl)
+    t = gamma * lam
+    a_m = np.array(m_bar, np.float64).reshape(m[0].shape)
+    a_z = np.zeros_like(a_m)
+    d_bar = np.zeros((plan.nt, plan.ntr))
+    for k in range(iters - 1, -1, -1):
+        c = a_m + (1.0 + betas[k]) * a_z
+        u_bar = np.where(np.abs(u[k]) > t, c, 0.0)
+        s = ops.forward(plan, u_bar, impl)
+        d_bar += gamma * s
+        a_z_new = u_bar - gamma * ops.adjoint(plan, s, impl)
+        a_m = -betas[k] * a_z
+        a_z = a_z_new
+    return m[iters], d_bar
