@@ -12,6 +12,12 @@ of d and m are inside the timed region.  L2 is flushed (256 MB write)
 between timed steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--workload gather|batch512]
+
+--workload batch512 times the batched form instead: 512 CMP cubes (nt = 1001,
+fold 200-3000, offsets in a 3 km disc over a random 90-360 degree azimuth
+sector, 64 curvatures x 24 azimuths) in one autotuned plan, one step = one
+50-iteration FISTA solve of every cube with its own step and threshold.
 
 Under torchrun each rank runs an independent replica on its own GPU (the
 path needs no communication); rank 0 prints one JSON line.
@@ -33,6 +39,10 @@ METRIC = ("AAHRT fwd+adj pairs/s and FISTA gathers/s on 1 GB300, %HBM roofline, 
 ITERS = 100
 WORKLOAD = ("paper-scale gather: nt=1001 dt=4ms, 2000 traces in a 3 km disc, "
             "100 q x 36 azimuths; one step = one 100-iteration FISTA solve")
+BATCH_ITERS = 50
+BATCH_WORKLOAD = ("512 CMP cubes: nt=1001 dt=4ms, fold 200-3000 in 90-360 degree sectors "
+                  "of a 3 km disc, 64 q x 24 azimuths, one autotuned plan; one step = one "
+                  "50-iteration FISTA solve of every cube (per-cube step and threshold)")
 
 
 def parse():
@@ -42,6 +52,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="gather", choices=["gather", "batch512"])
     return ap.parse_args()
 
 
@@ -171,21 +182,39 @@ def run_ours(args):
     from paper_2505_00387_gb300 import synthetic as syn
     from paper_2505_00387_gb300.plan import AahrtPlan
 
-    g = syn.config1(seed=1 + rank)
-    gp = AahrtPlan(**g.geom_kwargs())
+    batch = args.workload == "batch512"
+    if batch:
+        cubes = syn.config3(seed=3 + rank)
+        gp = AahrtPlan.batched(cubes, autotune=True)
+        d_np = np.concatenate([c.d.astype(np.float32).ravel() for c in cubes])
+        iters, pairs_per_step = BATCH_ITERS, BATCH_ITERS * len(cubes)
+    else:
+        g = syn.config1(seed=1 + rank)
+        gp = AahrtPlan(**g.geom_kwargs())
+        d_np = g.d.astype(np.float32).ravel()
+        iters, pairs_per_step = ITERS, ITERS
     info = gp.info
-    d = torch.from_numpy(g.d.astype(np.float32).ravel()).to(dev)
+    d = torch.from_numpy(d_np).to(dev)
     m = torch.zeros(gp.model_len, device=dev)
     stream = torch.cuda.current_stream()
 
-    # step length and lambda = 0.05 max|L^T d| from the device (setup, untimed)
-    _, si = gp.sparse_solve(d, 0.0, 0, m, lambda_rel=0.05, power_iters=30)
-    lam, gamma = float(getattr(si, "lambda")), float(si.gamma)
+    # step lengths and lambda = 0.05 max|L^T d| from the device (setup, untimed)
+    if batch:
+        cg = np.zeros(len(cubes))
+        cl = np.zeros(len(cubes))
+        gp.sparse_solve(d, 0.0, 0, m, lambda_rel=0.05, power_iters=30, per_cube=True,
+                        cube_gamma=cg, cube_lambda=cl, want_info=False)
+        lam, gamma = 0.0, 0.0
+        kw = dict(per_cube=True, cube_gamma=cg, cube_lambda=cl)
+    else:
+        _, si = gp.sparse_solve(d, 0.0, 0, m, lambda_rel=0.05, power_iters=30)
+        lam, gamma = float(getattr(si, "lambda")), float(si.gamma)
+        kw = dict(gamma=gamma)
 
     flush = torch.empty(256 * 1024 * 1024 // 4, device=dev)
 
     def step():
-        gp.sparse_solve(d, lam, ITERS, m, gamma=gamma, use_graph=True, want_info=False)
+        gp.sparse_solve(d, lam, iters, m, use_graph=True, want_info=False, **kw)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -219,16 +248,22 @@ def run_ours(args):
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     total_ms = float(t.item())
-    pairs = args.steps * ITERS * world
+    pairs = args.steps * pairs_per_step * world
     value = pairs / (total_ms / 1e3)
 
     # end to end: pinned host d in, pinned host m out, through the C ABI
-    d_host = torch.from_numpy(g.d.astype(np.float32).ravel()).pin_memory()
+    d_host = torch.from_numpy(d_np).pin_memory()
     m_host = torch.zeros(gp.model_len, dtype=torch.float32).pin_memory()
-    o = L.aahrt_solve_opts(0, 0, 0, 1, gamma, 0.0)
+    if batch:
+        import ctypes
+        dp = ctypes.POINTER(ctypes.c_double)
+        o = L.aahrt_solve_opts(0, 0, 0, 1, 0.0, 0.0, 1, cg.ctypes.data_as(dp),
+                               cl.ctypes.data_as(dp))
+    else:
+        o = L.aahrt_solve_opts(0, 0, 0, 1, gamma, 0.0)
 
     def step_e2e():
-        L.aahrt_sparse_solve(gp.handle, d_host.data_ptr(), lam, ITERS, m_host.data_ptr(), o,
+        L.aahrt_sparse_solve(gp.handle, d_host.data_ptr(), lam, iters, m_host.data_ptr(), o,
                              False, int(stream.cuda_stream))
 
     step_e2e()
@@ -244,7 +279,7 @@ def run_ours(args):
     gp.set_profiling(True)
     for _ in range(args.steps):
         flush.zero_()
-        gp.sparse_solve(d, lam, ITERS, m, gamma=gamma, use_graph=False, want_info=False)
+        gp.sparse_solve(d, lam, iters, m, use_graph=False, want_info=False, **kw)
     torch.cuda.synchronize()
     st_ms, st_n = gp.stage_times()
     gp.set_profiling(False)
@@ -254,17 +289,36 @@ def run_ours(args):
     if rank != 0:
         return
 
+    if batch:
+        folds = [c.ntr for c in cubes]
+        config = {"workload": BATCH_WORKLOAD, "ncube": len(cubes), "nt": cubes[0].nt,
+                  "dt": cubes[0].dt, "fold_min": min(folds), "fold_max": max(folds),
+                  "traces_total": int(sum(folds)), "nq": cubes[0].nq,
+                  "ntheta": cubes[0].ntheta, "fista_iters_per_step": iters,
+                  "nfft": info.nfft, "nbins": info.nbins,
+                  "autotuned": {"spread_width": info.spread_width,
+                                "theta_group": info.theta_group,
+                                "time_pairs": info.time_pairs},
+                  "l2": "inputs (%.1f GB spectra) far larger than L2, and flushed" %
+                        ((info.xspec_len + info.yspec_len) * 8 / 1e9),
+                  "parallelism": f"replicas x{world}"}
+    else:
+        config = {"workload": WORKLOAD, "nt": g.nt, "dt": g.dt, "ntr": g.ntr, "nq": g.nq,
+                  "ntheta": g.ntheta, "fista_iters_per_step": iters, "nfft": info.nfft,
+                  "nbins": info.nbins, "spread_width": info.spread_width,
+                  "l2": "flushed between timed steps (256 MB write)",
+                  "parallelism": f"replicas x{world}"}
     sb = stage_bytes(info)
     names = L.STAGE_NAMES
     per_launch = [st_ms[i] / st_n[i] if st_n[i] else 0.0 for i in range(L.AAHRT_NSTAGES)]
     top = max(range(6), key=lambda i: st_ms[i])
     peak, peak_kind = peaks()
     achieved = sb[top] / (per_launch[top] * 1e-3) / 1e9
-    iter_ms = sum(st_ms[:6]) / (args.steps * ITERS)
+    iter_ms = sum(st_ms[:6]) / (args.steps * iters)
     iter_bytes = sum(sb[:6])
     kernel_names = ["r2c_kernel", "slice_fwd_kernel", "c2r_kernel", "r2c_kernel",
                     "slice_adj_kernel", "c2r_kernel"]
-    tr = traffic_record(names[top])
+    tr = None if batch else traffic_record(names[top])
     line = {
         "metric": METRIC,
         "value": round(value, 3),
@@ -278,12 +332,8 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nt": g.nt, "dt": g.dt, "ntr": g.ntr, "nq": g.nq,
-                   "ntheta": g.ntheta, "fista_iters_per_step": ITERS, "nfft": info.nfft,
-                   "nbins": info.nbins, "spread_width": info.spread_width,
-                   "l2": "flushed between timed steps (256 MB write)",
-                   "parallelism": f"replicas x{world}"},
-        "gathers_per_s": round(value / ITERS, 4),
+        "config": config,
+        "gathers_per_s": round(value / iters, 4),
         "e2e": {"value": round(e2e_value, 3), "unit": "pairs/s",
                 "h2d_bytes_per_step": 4 * gp.data_len, "d2h_bytes_per_step": 4 * gp.model_len},
         "gpu_launches": launches,
@@ -305,7 +355,10 @@ def run_ours(args):
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"], line["err_vs_fp64"] = cpu_baseline(g, gp, d, dev)
+        if batch:
+            line["cpu_baseline"], line["err_vs_fp64"] = cpu_baseline_batch(cubes, gp, d, dev)
+        else:
+            line["cpu_baseline"], line["err_vs_fp64"] = cpu_baseline(g, gp, d, dev)
     print(json.dumps(line), flush=True)
 
 
@@ -337,6 +390,42 @@ def cpu_baseline(g, gp, d_dev, dev, pairs=2):
     cb = {"value": round(pairs / el, 5), "unit": "pairs/s", "cores": ops.threads(),
           "kind": "oracle",
           "sample": f"{pairs} forward+adjoint pairs of the full gather, FP64, "
+                    f"{el:.1f} s wall"}
+    return cb, err
+
+
+def cpu_baseline_batch(cubes, gp, d_dev, dev):
+    """The FP64 checker on one forward+adjoint pair of the median-fold cube
+    (on the batch's shared time plan), and the GPU error on that cube."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from oracle import ops
+
+    folds = np.array([c.ntr for c in cubes])
+    i = int(np.argsort(folds)[len(folds) // 2])
+    c = cubes[i]
+    r2max = max(float(np.max(x.hx ** 2 + x.hy ** 2)) for x in cubes)
+    p = oracle.make_plan(**c.geom_kwargs(), r2max=r2max)
+    rng = np.random.default_rng(124)
+    m_all = rng.standard_normal(gp.model_len).astype(np.float32)
+    msz = c.ntau * c.nq * c.ntheta
+    mr = m_all[i * msz:(i + 1) * msz].astype(np.float64).reshape(c.ntau, c.nq, c.ntheta)
+    t0 = time.perf_counter()
+    d_or = ops.forward(p, mr)
+    m_or = ops.adjoint(p, c.d)
+    el = time.perf_counter() - t0
+    d_gpu = gp.forward(torch.from_numpy(m_all).to(dev)).cpu().numpy().astype(np.float64)
+    m_gpu = gp.adjoint(d_dev).cpu().numpy().astype(np.float64)
+    off = sum(x.nt * x.ntr for x in cubes[:i])
+    d_gpu = d_gpu[off:off + c.nt * c.ntr].reshape(d_or.shape)
+    m_gpu = m_gpu[i * msz:(i + 1) * msz].reshape(m_or.shape)
+    err = {"cube": i, "forward_rel_l2": float(np.linalg.norm(d_gpu - d_or) / np.linalg.norm(d_or)),
+           "adjoint_rel_l2": float(np.linalg.norm(m_gpu - m_or) / np.linalg.norm(m_or))}
+    cb = {"value": round(1.0 / el, 5), "unit": "pairs/s", "cores": ops.threads(),
+          "kind": "oracle",
+          "sample": f"1 forward+adjoint pair of cube {i} (median fold {c.ntr}), FP64, "
                     f"{el:.1f} s wall"}
     return cb, err
 

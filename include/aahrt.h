@@ -101,6 +101,11 @@ typedef struct {
     int ngather;        /* gathers sharing this geometry; 0 = 1 */
     double sigma_t;     /* FFT frame oversampling of the time axis; 0 = 2 */
     double fmax;        /* highest kept stretched frequency in 1/s^2; 0 = all */
+    int time_pairs;     /* column pairs per time-kernel block (1, 2, 4 or 8);
+                           0 = automatic (8192 / Nfft, clamped) */
+    int autotune;       /* 1: pick spread_width, theta_group and time_pairs
+                           at plan creation (see aahrt_plan_create); fields
+                           set explicitly above are kept */
 } aahrt_opts;
 
 /* What a plan chose (filled by aahrt_plan_query). */
@@ -121,6 +126,9 @@ typedef struct {
     long long xspec_len;     /* complex values of a model spectrum X[g][k][q][theta] */
     long long yspec_len;     /* complex values of a data spectrum Y[g][k][trace] */
     long long workspace_bytes;
+    int time_pairs;          /* column pairs per time-kernel block */
+    int autotuned;           /* 1 if the autotuner chose the tiles above */
+    double tune_ms;          /* autotuner: best forward+adjoint time of its trial batch */
 } aahrt_plan_info;
 
 /* Create a plan on the current CUDA device: validates the geometry,
@@ -128,7 +136,16 @@ typedef struct {
  * azimuth binning (eq. thli), and allocates the device workspace.  With
  * opts->ngather = G > 1 the plan serves G gathers on this one geometry,
  * stored back to back in m and d.  On success *out owns device memory until
- * aahrt_plan_destroy. */
+ * aahrt_plan_destroy.
+ *
+ * Autotuning (opts->autotune = 1; not part of the paper's method): the
+ * spreading width is the smallest whose measured forward error against the
+ * widest kernel (12 taps) on a seeded random model stays below 2e-6
+ * relative, then every candidate (theta_group, time_pairs) pair is built and
+ * timed (median of 3 forward+adjoint pairs, CUDA events) on a trial batch of
+ * at most 16 of the cubes or gathers, and the fastest is kept.  Explicitly
+ * set fields are not tuned.  Tuning synchronises the device and needs room
+ * for two plans of the trial batch at once. */
 int aahrt_plan_create(aahrt_plan **out, const aahrt_geom *geom,
                       const aahrt_opts *opts);
 
@@ -176,6 +193,17 @@ typedef struct {
     int use_graph;       /* 1: capture the iterations in a CUDA graph; 0 = eager */
     double gamma;        /* step length; <= 0: 0.95 / (power estimate of ||L||^2) */
     double lambda_rel;   /* > 0: lambda = lambda_rel * max|L^T d| (lambda ignored) */
+    int per_cube;        /* 1: every cube of a batched plan (every gather of a
+                            multi-gather plan) is an independent problem with
+                            its own step and threshold; the power iteration
+                            and max|L^T d| are then taken per cube */
+    double *cube_gamma;  /* per_cube: NULL or host array [ncube]; entries > 0 are
+                            used as that cube's step, the others (and all when
+                            NULL, or when gamma > 0: gamma for every cube) are
+                            estimated; on return holds the steps used */
+    double *cube_lambda; /* per_cube: NULL or host array [ncube]; on entry the
+                            cube's lambda (lambda_rel > 0 overrides), on return
+                            the lambda used; NULL: lambda (or lambda_rel) for all */
 } aahrt_solve_opts;
 
 typedef struct {
@@ -191,12 +219,36 @@ typedef struct {
  *   m <- soft(z + gamma L^T (d - L z), gamma*lambda)   (eqs. ISTA, soft)
  * with z = m (ISTA) or the FISTA extrapolation of m.  d: data_len floats;
  * m: model_len floats, in/out.  opts and info may be NULL.  When info is
- * non-NULL, or gamma/lambda must be estimated, the call synchronises the
- * stream.  For batched and multi-gather plans one gamma and one lambda serve
- * every cube. */
+ * non-NULL, gamma/lambda must be estimated, or per_cube is set, the call
+ * synchronises the stream.  For batched and multi-gather plans one gamma and
+ * one lambda serve every cube unless opts->per_cube is set; then info holds
+ * cube 0's gamma and lambda, the residual and l1 norms over all cubes and
+ * the sum of the cubes' objectives. */
 int aahrt_sparse_solve(aahrt_plan *plan, const float *d, float lambda,
                        int iters, float *m, const aahrt_solve_opts *opts,
                        aahrt_solve_info *info, void *stream);
+
+/* Derivative of the unrolled sparse solve (configuration of Sec. 4 used as a
+ * differentiable layer).  With m^n(d) the result of `iters` iterations of
+ * aahrt_sparse_solve from m^0 = 0 at the given gamma and lambda (FISTA, or
+ * ISTA when ista != 0), computes the vector-Jacobian product
+ *   d_bar = (d m^n / d d)^T m_bar
+ * and, when m_out is non-NULL, m^n itself.  The shrinkage of eq. soft has
+ * slope 1 where |z + gamma g| > gamma*lambda and 0 elsewhere (its kink is
+ * given slope 0).  gamma (> 0) and lambda (>= 0) are fixed inputs here:
+ * their estimation from d (power iteration, lambda_rel) is not
+ * differentiated.  The forward iterates are checkpointed every `checkpoint`
+ * iterations (<= 0: 10) and each segment is recomputed before its reverse
+ * sweep, so one call costs about 3*iters operator pairs and holds
+ * 2*ceil(iters/checkpoint) + checkpoint + 6 model-sized buffers and one
+ * data-sized buffer of plan-owned workspace (grown on demand, freed with the
+ * plan; growing it synchronises the device).
+ * d (data_len), m_bar (model_len), d_bar (data_len) and m_out (model_len):
+ * device memory, 16-byte aligned, not overlapping.  Stream-ordered, no
+ * synchronisation otherwise. */
+int aahrt_fista_vjp(aahrt_plan *plan, const float *d, const float *m_bar,
+                    float lambda, float gamma, int iters, int ista,
+                    int checkpoint, float *m_out, float *d_bar, void *stream);
 
 /* Uniform curvature axis for a slowness range: q0 = pmin^2 and
  * dq = (pmax^2 - pmin^2)/(nq - 1) (curvature is squared slowness, Sec. 2). */

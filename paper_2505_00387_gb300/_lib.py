@@ -33,7 +33,8 @@ class aahrt_geom(ctypes.Structure):
 
 class aahrt_opts(ctypes.Structure):
     _fields_ = [("interp_kind", c_int), ("spread_width", c_int), ("theta_group", c_int),
-                ("ngather", c_int), ("sigma_t", c_double), ("fmax", c_double)]
+                ("ngather", c_int), ("sigma_t", c_double), ("fmax", c_double),
+                ("time_pairs", c_int), ("autotune", c_int)]
 
 
 class aahrt_plan_info(ctypes.Structure):
@@ -42,12 +43,15 @@ class aahrt_plan_info(ctypes.Structure):
                 ("ngather", c_int), ("ds", c_double), ("rho", c_double), ("beta", c_double),
                 ("model_len", c_longlong), ("data_len", c_longlong),
                 ("xspec_len", c_longlong), ("yspec_len", c_longlong),
-                ("workspace_bytes", c_longlong)]
+                ("workspace_bytes", c_longlong), ("time_pairs", c_int), ("autotuned", c_int),
+                ("tune_ms", c_double)]
 
 
 class aahrt_solve_opts(ctypes.Structure):
     _fields_ = [("ista", c_int), ("warm_start", c_int), ("power_iters", c_int),
-                ("use_graph", c_int), ("gamma", c_double), ("lambda_rel", c_double)]
+                ("use_graph", c_int), ("gamma", c_double), ("lambda_rel", c_double),
+                ("per_cube", c_int), ("cube_gamma", POINTER(c_double)),
+                ("cube_lambda", POINTER(c_double))]
 
 
 class aahrt_solve_info(ctypes.Structure):
@@ -76,6 +80,8 @@ _SIGS = {
                                    POINTER(aahrt_solve_opts), POINTER(aahrt_solve_info),
                                    c_void_p]),
     "aahrt_apply_stage": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+    "aahrt_fista_vjp": (c_int, [c_void_p, c_void_p, c_void_p, c_float, c_float, c_int, c_int,
+                                c_int, c_void_p, c_void_p, c_void_p]),
     "aahrt_forward_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "aahrt_q_from_slowness": (c_int, [c_double, c_double, c_int, POINTER(c_double),
                                       POINTER(c_double)]),
@@ -163,6 +169,14 @@ def aahrt_sparse_solve(h, d_ptr: int, lam: float, iters: int, m_ptr: int,
                                     c_void_p(stream)),
           "aahrt_sparse_solve")
     return info
+
+
+def aahrt_fista_vjp(h, d_ptr: int, mbar_ptr: int, lam: float, gamma: float, iters: int,
+                    ista: bool, checkpoint: int, mout_ptr, dbar_ptr: int, stream: int = 0):
+    check(load().aahrt_fista_vjp(h, c_void_p(d_ptr), c_void_p(mbar_ptr), c_float(lam),
+                                 c_float(gamma), int(iters), int(bool(ista)), int(checkpoint),
+                                 c_void_p(mout_ptr) if mout_ptr else None, c_void_p(dbar_ptr),
+                                 c_void_p(stream)), "aahrt_fista_vjp")
 
 
 def aahrt_apply_stage(h, stage: int, in_ptr: int, out_ptr: int, stream: int = 0):

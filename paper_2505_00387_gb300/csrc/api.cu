@@ -13,6 +13,14 @@ namespace aahrt {
 
 int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
                const aahrt_opts *opts);
+int autotune_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
+                  const aahrt_opts *opts);
+
+static int make_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
+                     const aahrt_opts *opts) {
+    if (opts && opts->autotune) return autotune_plan(out, ncube, ndist, geoms, opts);
+    return build_plan(out, ncube, ndist, geoms, opts);
+}
 void free_plan(Plan *p);
 void plan_info(const Plan &p, aahrt_plan_info *info);
 int collect_profile(Plan &p);
@@ -66,6 +74,57 @@ __global__ void normalize_kernel(const float *__restrict__ x, float *__restrict_
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
         y[i] = x[i] * s;
+}
+
+// Per-cube (segmented) versions.  Cube c = blockIdx.y owns elements
+// [c*seg, (c+1)*seg) when seg > 0, else [off[c], off[c+1]).
+// kind 0: acc[c] += sum x^2; 1: += sum |x|; 2: += sum x*y; 3: max |x| (float bits)
+__global__ void seg_reduce_kernel(const float *__restrict__ x, const float *__restrict__ y,
+                                  long long seg, const long long *__restrict__ off, int kind,
+                                  double *acc) {
+    __shared__ double part[32];
+    const int c = blockIdx.y;
+    const long long b = seg > 0 ? c * seg : off[c];
+    const long long e = seg > 0 ? b + seg : off[c + 1];
+    double s = 0.0;
+    float mx = 0.f;
+    for (long long i = b + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < e;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float a = x[i];
+        if (kind == 3) mx = fmaxf(mx, fabsf(a));
+        else s += kind == 0 ? (double)a * a : (kind == 1 ? fabs((double)a) : (double)a * y[i]);
+    }
+    if (kind == 3) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
+        if ((threadIdx.x & 31) == 0)
+            atomicMax(reinterpret_cast<unsigned *>(acc + c), __float_as_uint(mx));
+        return;
+    }
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
+        s = warp_sum(s);
+        if (threadIdx.x == 0) atomicAdd(acc + c, s);
+    }
+}
+
+// y = x / sqrt(ss[c]) on cube c's model block; a cube with ss = 0 gets the
+// constant unit vector (a valid start of its power iteration).
+__global__ void seg_normalize_kernel(const float *__restrict__ x, float *__restrict__ y,
+                                     long long seg, const double *__restrict__ ss) {
+    const int c = blockIdx.y;
+    const double v = ss[c];
+    const bool zero = !(v > 0.0);
+    const float sc = zero ? 0.f : (float)(1.0 / sqrt(v));
+    const float cst = (float)(1.0 / sqrt((double)seg));
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < seg;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long j = c * seg + i;
+        y[j] = zero ? cst : x[j] * sc;
+    }
 }
 
 static int reduce_grid(long long n) {
@@ -216,19 +275,6 @@ static int finish_args(const Staged &s, cudaStream_t st) {
     return e ? cuda_fail(e, "copy output to host") : AAHRT_OK;
 }
 
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        cudaGetDevice(&prev);
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        cudaGetDevice(&cur);
-        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
-    }
-};
-
 static int ensure_solver_ws(Plan &p) {
     cudaError_t e;
     if (!p.z && (e = cudaMalloc((void **)&p.z, p.model_len * sizeof(float))))
@@ -261,13 +307,121 @@ static int read_scalars(Plan &p, double *h, cudaStream_t st) {
 // per iteration one forward with the residual fused (rb = db - L zb) and one
 // adjoint with the shrinkage/momentum update fused.
 static int run_iterations(Plan &p, int iters, float gamma, float thresh,
-                          const std::vector<double> &betas, cudaStream_t st) {
+                          const std::vector<double> &betas, const float2 *cube_gt,
+                          cudaStream_t st) {
     for (int it = 0; it < iters; ++it) {
         int rc = apply_forward(p, p.zb, p.rb, st, EPI_RESIDUAL, p.db, true);
         if (rc) return rc;
-        FistaArgs fa{p.mb, p.zb, gamma, thresh, (float)betas[it]};
+        FistaArgs fa{p.mb, p.zb, gamma, thresh, (float)betas[it], cube_gt};
         rc = apply_adjoint(p, p.rb, nullptr, st, EPI_FISTA, fa, true);
         if (rc) return rc;
+    }
+    return AAHRT_OK;
+}
+
+enum { CA_SS = 0, CA_DOT = 1, CA_MAX = 2, CA_L1 = 3, CA_SLOTS = 4 };
+
+static int ensure_cube_ws(Plan &p) {
+    cudaError_t e;
+    if (!p.cube_gt && (e = cudaMalloc((void **)&p.cube_gt, p.ncube * sizeof(float2))))
+        return cuda_fail(e, "alloc per-cube scalars");
+    if (!p.cube_acc &&
+        (e = cudaMalloc((void **)&p.cube_acc, CA_SLOTS * p.ncube * sizeof(double))))
+        return cuda_fail(e, "alloc per-cube scalars");
+    if (!p.dseg) {
+        std::vector<long long> off(p.ncube + 1);
+        for (int c = 0; c < p.ncube; ++c) off[c] = p.data_off[c];
+        off[p.ncube] = p.data_len;
+        if ((e = cudaMalloc((void **)&p.dseg, off.size() * sizeof(long long))))
+            return cuda_fail(e, "alloc per-cube scalars");
+        if ((e = cudaMemcpy(p.dseg, off.data(), off.size() * sizeof(long long),
+                            cudaMemcpyHostToDevice)))
+            return cuda_fail(e, "upload cube offsets");
+    }
+    return AAHRT_OK;
+}
+
+// acc[slot][c] (re)computed over every cube's model (model = true) or data block
+static cudaError_t seg_reduce(Plan &p, const float *x, const float *y, bool model, int kind,
+                              int slot, cudaStream_t st) {
+    double *acc = p.cube_acc + (size_t)slot * p.ncube;
+    cudaError_t e = cudaMemsetAsync(acc, 0, p.ncube * sizeof(double), st);
+    if (e) return e;
+    const long long seg = model ? p.model_len / p.ncube : 0;
+    const long long per = model ? seg : (p.data_len + p.ncube - 1) / p.ncube;
+    const int gx = (int)std::max<long long>(1, std::min<long long>((per + 2047) / 2048, 64));
+    seg_reduce_kernel<<<dim3(gx, p.ncube), 256, 0, st>>>(x, y, seg, p.dseg, kind, acc);
+    p.launches[6]++;
+    return cudaGetLastError();
+}
+
+static int read_cube_acc(Plan &p, std::vector<double> *h, cudaStream_t st) {
+    h->resize((size_t)CA_SLOTS * p.ncube);
+    cudaError_t e = cudaMemcpyAsync(h->data(), p.cube_acc, h->size() * sizeof(double),
+                                    cudaMemcpyDeviceToHost, st);
+    if (!e) e = cudaStreamSynchronize(st);
+    return e ? cuda_fail(e, "read per-cube scalars") : AAHRT_OK;
+}
+
+static float acc_bits_to_float(double v) {
+    unsigned bits;
+    std::memcpy(&bits, &v, sizeof bits);
+    float f;
+    std::memcpy(&f, &bits, sizeof f);
+    return f;
+}
+
+// Per-cube step and threshold: lambda_c = lambda_rel max|L^T d_c| (or the
+// given value), gamma_c = 0.95 / (power estimate of ||L_c||^2) unless given.
+static int cube_params(Plan &p, const float *d, float lambda, const aahrt_solve_opts &o,
+                       std::vector<double> *gam, std::vector<double> *lam, cudaStream_t st) {
+    const int nc = p.ncube;
+    gam->assign(nc, 0.0);
+    lam->assign(nc, (double)lambda);
+    bool need_gamma = false;
+    for (int c = 0; c < nc; ++c) {
+        if (o.gamma > 0.0) (*gam)[c] = o.gamma;
+        else if (o.cube_gamma && o.cube_gamma[c] > 0.0) (*gam)[c] = o.cube_gamma[c];
+        else need_gamma = true;
+        if (o.cube_lambda && !(o.lambda_rel > 0.0)) (*lam)[c] = o.cube_lambda[c];
+    }
+    if (!need_gamma && !(o.lambda_rel > 0.0)) return AAHRT_OK;
+    int rc;
+    cudaError_t e;
+    std::vector<double> h;
+    const long long seg = p.model_len / nc;
+    const int gx = (int)std::max<long long>(1, std::min<long long>((seg + 2047) / 2048, 64));
+    if ((rc = apply_adjoint(p, d, p.v, st))) return rc;
+    if (o.lambda_rel > 0.0) {
+        if ((e = seg_reduce(p, p.v, nullptr, true, 3, CA_MAX, st)))
+            return cuda_fail(e, "absmax launch");
+        if ((rc = read_cube_acc(p, &h, st))) return rc;
+        for (int c = 0; c < nc; ++c)
+            (*lam)[c] = o.lambda_rel * (double)acc_bits_to_float(h[(size_t)CA_MAX * nc + c]);
+    }
+    if (!need_gamma) return AAHRT_OK;
+    const int piters = o.power_iters > 0 ? o.power_iters : 30;
+    if ((e = seg_reduce(p, p.v, nullptr, true, 0, CA_SS, st))) return cuda_fail(e, "norm launch");
+    seg_normalize_kernel<<<dim3(gx, nc), 256, 0, st>>>(p.v, p.v, seg, p.cube_acc + CA_SS * nc);
+    p.launches[6]++;
+    for (int it = 0; it < piters; ++it) {
+        if ((rc = apply_forward(p, p.v, p.r, st))) return rc;
+        if ((rc = apply_adjoint(p, p.r, p.z, st))) return rc;
+        if ((e = seg_reduce(p, p.v, p.z, true, 2, CA_DOT, st)) ||
+            (e = seg_reduce(p, p.z, nullptr, true, 0, CA_SS, st)))
+            return cuda_fail(e, "power iteration launch");
+        seg_normalize_kernel<<<dim3(gx, nc), 256, 0, st>>>(p.z, p.v, seg,
+                                                          p.cube_acc + CA_SS * nc);
+        p.launches[6]++;
+    }
+    if ((e = cudaGetLastError())) return cuda_fail(e, "power iteration");
+    if ((rc = read_cube_acc(p, &h, st))) return rc;
+    for (int c = 0; c < nc; ++c) {
+        if ((*gam)[c] > 0.0) continue;
+        const double s2 = h[(size_t)CA_DOT * nc + c];
+        if (!(s2 > 0.0) || !std::isfinite(s2))
+            return set_error(AAHRT_ERR_NONFINITE, "power iteration of cube %d gave %g", c, s2);
+        (*gam)[c] = 0.95 / s2;
     }
     return AAHRT_OK;
 }
@@ -280,7 +434,30 @@ static int solve(Plan &p, const float *d, float lambda, int iters, float *m,
     double gamma = o.gamma;
     double lam = lambda;
     double h[SC_COUNT];
-    if (gamma <= 0.0 || o.lambda_rel > 0.0) {
+    const bool per_cube = o.per_cube != 0;
+    std::vector<double> cgam, clam;
+    if (per_cube) {
+        if ((rc = ensure_cube_ws(p))) return rc;
+        if ((rc = cube_params(p, d, lambda, o, &cgam, &clam, st))) return rc;
+        std::vector<float2> gt(p.ncube);
+        for (int c = 0; c < p.ncube; ++c) {
+            if (!(cgam[c] > 0.0) || !std::isfinite(cgam[c]) || !(clam[c] >= 0.0) ||
+                !std::isfinite(clam[c]))
+                return set_error(AAHRT_ERR_INVALID_ARG, "cube %d: gamma (%g) and lambda (%g) "
+                                 "must be finite, gamma > 0, lambda >= 0", c, cgam[c], clam[c]);
+            gt[c] = make_float2((float)cgam[c], (float)(cgam[c] * clam[c]));
+        }
+        if ((e = cudaMemcpyAsync(p.cube_gt, gt.data(), gt.size() * sizeof(float2),
+                                 cudaMemcpyHostToDevice, st)) ||
+            (e = cudaStreamSynchronize(st)))
+            return cuda_fail(e, "upload per-cube scalars");
+        for (int c = 0; c < p.ncube; ++c) {
+            if (o.cube_gamma) o.cube_gamma[c] = cgam[c];
+            if (o.cube_lambda) o.cube_lambda[c] = clam[c];
+        }
+        gamma = cgam[0];
+        lam = clam[0];
+    } else if (gamma <= 0.0 || o.lambda_rel > 0.0) {
         // L^T d, for lambda_rel * max|L^T d| and as the power iteration's start
         if ((rc = apply_adjoint(p, d, p.v, st))) return rc;
         if (o.lambda_rel > 0.0) {
@@ -347,10 +524,15 @@ static int solve(Plan &p, const float *d, float lambda, int iters, float *m,
         }
     }
     const float fg = (float)gamma, fth = (float)(gamma * lam);
+    const float2 *cgt = per_cube ? p.cube_gt : nullptr;
     if (iters > 0) {
         if (o.use_graph && !p.profiling) {
             char key[256];
-            snprintf(key, sizeof key, "%d/%.9g/%.9g/%d", iters, (double)fg, (double)fth, o.ista);
+            if (per_cube)
+                snprintf(key, sizeof key, "%d/cube/%d", iters, o.ista);
+            else
+                snprintf(key, sizeof key, "%d/%.9g/%.9g/%d", iters, (double)fg, (double)fth,
+                         o.ista);
             if (!p.gexec || p.gkey != key) {
                 if (p.gexec) { cudaGraphExecDestroy(p.gexec); p.gexec = nullptr; }
                 cudaStream_t cs;
@@ -361,7 +543,7 @@ static int solve(Plan &p, const float *d, float lambda, int iters, float *m,
                 cudaGraph_t graph = nullptr;
                 e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
                 if (!e) {
-                    rc = run_iterations(p, iters, fg, fth, betas, cs);
+                    rc = run_iterations(p, iters, fg, fth, betas, cgt, cs);
                     cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
                     if (!e) e = e2;
                 }
@@ -383,13 +565,33 @@ static int solve(Plan &p, const float *d, float lambda, int iters, float *m,
             // each iteration launches one kernel per operator stage
             for (int s = 0; s < 6; ++s) p.launches[s] += iters;
         } else {
-            if ((rc = run_iterations(p, iters, fg, fth, betas, st))) return rc;
+            if ((rc = run_iterations(p, iters, fg, fth, betas, cgt, st))) return rc;
         }
     }
 
     if ((e = reblock(p, true, p.mb, m, false, st))) return cuda_fail(e, "reblock model");
 
-    if (info) {
+    if (info && per_cube) {
+        if ((rc = apply_forward(p, m, p.r, st, EPI_RESIDUAL, d))) return rc;
+        if ((e = seg_reduce(p, p.r, nullptr, false, 0, CA_SS, st)) ||
+            (e = seg_reduce(p, m, nullptr, true, 1, CA_L1, st)))
+            return cuda_fail(e, "norm launch");
+        std::vector<double> hc;
+        if ((rc = read_cube_acc(p, &hc, st))) return rc;
+        double ss = 0.0, l1 = 0.0, obj = 0.0;
+        for (int c = 0; c < p.ncube; ++c) {
+            const double sc = hc[(size_t)CA_SS * p.ncube + c], lc = hc[(size_t)CA_L1 * p.ncube + c];
+            ss += sc;
+            l1 += lc;
+            obj += 0.5 * sc + clam[c] * lc;
+        }
+        info->iters = iters;
+        info->gamma = gamma;
+        info->lambda = lam;
+        info->resid_norm = std::sqrt(ss);
+        info->l1_norm = l1;
+        info->objective = obj;
+    } else if (info) {
         if ((rc = apply_forward(p, m, p.r, st, EPI_RESIDUAL, d))) return rc;
         if ((e = reduce(p, p.r, nullptr, p.data_len, 0, SC_SUMSQ, st)))
             return cuda_fail(e, "norm launch");
@@ -417,7 +619,7 @@ int aahrt_plan_create(aahrt_plan **out, const aahrt_geom *geom, const aahrt_opts
     *out = nullptr;
     const int G = (opts && opts->ngather > 0) ? opts->ngather : 1;
     Plan *p = nullptr;
-    int rc = build_plan(&p, G, 1, geom, opts);
+    int rc = make_plan(&p, G, 1, geom, opts);
     if (rc) return rc;
     *out = new aahrt_plan{p};
     return AAHRT_OK;
@@ -431,7 +633,7 @@ int aahrt_plan_create_batched(aahrt_plan **out, int ncube, const aahrt_geom *geo
     if (opts && opts->ngather > 1)
         return set_error(AAHRT_ERR_INVALID_ARG, "ngather > 1 is for aahrt_plan_create");
     Plan *p = nullptr;
-    int rc = build_plan(&p, ncube, ncube, geoms, opts);
+    int rc = make_plan(&p, ncube, ncube, geoms, opts);
     if (rc) return rc;
     *out = new aahrt_plan{p};
     return AAHRT_OK;

@@ -52,7 +52,7 @@ struct ColGroup {
     long long spec_off;  // complex offset of its first column in the spectrum
     int ld_real, ld_spec;  // row strides (elements)
     int ncol;
-    int pad_;
+    int cube;            // cube (or gather) the columns belong to
 };
 
 // Resampler tables.  Output row o of the stretch S (or its undoing U) sits
@@ -81,7 +81,13 @@ struct FistaArgs {
     float gamma;
     float thresh;    // gamma * lambda
     float beta;      // momentum weight (t_k - 1)/t_{k+1}
+    const float2 *cube_gt;   // per-cube (gamma, thresh) overriding the two above, or null
 };
+
+// x * max(1 - t/|x|, 0) of eq. soft, written without the division
+__device__ __forceinline__ float soft_threshold(float x, float t) {
+    return copysignf(fmaxf(fabsf(x) - t, 0.f), x);
+}
 
 struct Plan {
     int device = 0;
@@ -137,6 +143,14 @@ struct Plan {
     float *zb = nullptr, *mb = nullptr, *rb = nullptr, *db = nullptr;   // column-blocked
     double *scal = nullptr;        // device scalars of the solver
     float *stage_m = nullptr, *stage_d = nullptr;   // staging of host buffers
+    float *vjp_ws = nullptr;       // workspace of the unrolled-solve derivative
+    size_t vjp_bytes = 0;
+    float2 *cube_gt = nullptr;     // per-cube (gamma, gamma*lambda) of a per-cube solve
+    double *cube_acc = nullptr;    // per-cube FP64 accumulators [slot][ncube]
+    long long *dseg = nullptr;     // data offsets of the cubes (ncube + 1 entries)
+    // tiles
+    bool autotuned = false;
+    double tune_ms = 0;
     // cached graph of the last solve
     cudaGraphExec_t gexec = nullptr;
     std::string gkey;
@@ -181,6 +195,20 @@ void prof_end(Plan &p, cudaStream_t st);
 
 // pointer checks of the C ABI
 int check_dev_ptr(const void *ptr, const char *name);
+
+// Makes the plan's device current for the scope of a C entry point.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
 
 // operator application used by the C ABI and the solver
 int apply_forward(Plan &p, const float *m, float *d, cudaStream_t st,

@@ -182,7 +182,8 @@ void free_plan(Plan *p) {
     void *ptrs[] = {p->tw_t, p->tw_q, p->dec, p->geo, p->groups, p->slice_start, p->counters,
                     p->cg_model, p->cg_data, p->cg_model_blk, p->cg_data_blk, p->posS,
                     p->posU, p->rngST, p->rngUT, p->X, p->Y, p->z, p->r, p->v, p->scal,
-                    p->stage_m, p->stage_d, p->zb, p->mb, p->rb, p->db};
+                    p->stage_m, p->stage_d, p->zb, p->mb, p->rb, p->db, p->vjp_ws,
+                    p->cube_gt, p->cube_acc, p->dseg};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     cudaSetDevice(cur);
@@ -241,6 +242,9 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
         return set_error(AAHRT_ERR_INVALID_ARG, "sigma_t must be 0 (default) or >= 1");
     if (opts.fmax < 0.0 || opts.theta_group < 0 || opts.ngather < 0)
         return set_error(AAHRT_ERR_INVALID_ARG, "fmax, theta_group, ngather must be >= 0");
+    if (opts.time_pairs != 0 && opts.time_pairs != 1 && opts.time_pairs != 2 &&
+        opts.time_pairs != 4 && opts.time_pairs != 8)
+        return set_error(AAHRT_ERR_INVALID_ARG, "time_pairs must be 0, 1, 2, 4 or 8");
 
     Plan *p = new Plan();
     cudaGetDevice(&p->device);
@@ -286,7 +290,7 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
     if (p->fmax > 0.0)
         p->kmax = std::min(p->kmax, (int)std::floor(p->fmax * p->nfft * p->ds));
     p->nbins = p->kmax + 1;
-    p->pairs = std::max(1, std::min(8, 8192 / p->nfft));
+    p->pairs = opts.time_pairs > 0 ? opts.time_pairs : std::max(1, std::min(8, 8192 / p->nfft));
     p->lp = ilog2(p->pairs);
 
     // ----------------------------------------------------- q spreading
@@ -398,7 +402,7 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
             q.ld_real = (int)C;
             q.ld_spec = (int)C;
             q.ncol = (int)std::min<long long>(cpg, C - c0);
-            q.pad_ = 0;
+            q.cube = c;
             cgm.push_back(q);
         }
     for (int c = 0; c < ncube; ++c)
@@ -409,7 +413,7 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
             q.ld_real = p->ntr[c];
             q.ld_spec = p->ntr[c];
             q.ncol = std::min(cpg, p->ntr[c] - h0);
-            q.pad_ = 0;
+            q.cube = c;
             cgd.push_back(q);
         }
     p->ncg_model = (int)cgm.size();
@@ -521,7 +525,7 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
         (int)p->smem_sadj > max_smem) {
         rc_fail = set_error(AAHRT_ERR_UNSUPPORTED,
                             "shared memory per block (%zu / %zu bytes) exceeds %d; lower "
-                            "theta_group", smem_r2c, p->smem_sfwd, max_smem);
+                            "theta_group or time_pairs", smem_r2c, p->smem_sfwd, max_smem);
         free_plan(p);
         return rc_fail;
     }
@@ -553,6 +557,9 @@ void plan_info(const Plan &p, aahrt_plan_info *info) {
     info->xspec_len = p.x_len;
     info->yspec_len = p.y_len;
     info->workspace_bytes = (p.x_len + p.y_len) * (long long)sizeof(float2);
+    info->time_pairs = p.pairs;
+    info->autotuned = p.autotuned ? 1 : 0;
+    info->tune_ms = p.tune_ms;
 }
 
 // ----------------------------------------------------------- profiling

@@ -161,11 +161,6 @@ r2c_kernel(const float *__restrict__ in, float2 *__restrict__ out,
     }
 }
 
-__device__ __forceinline__ float soft_threshold(float x, float t) {
-    // x * max(1 - t/|x|, 0) of eq. soft, written without the division
-    return copysignf(fmaxf(fabsf(x) - t, 0.f), x);
-}
-
 template <int LP, int INTERP, bool TRANS, int EPI>
 __global__ void __launch_bounds__(kThreadsTime, 2)
 c2r_kernel(const float2 *__restrict__ in, float *__restrict__ out,
@@ -257,6 +252,12 @@ c2r_kernel(const float2 *__restrict__ in, float *__restrict__ out,
                 if (c < nc) out[o + c] = dv[c] - g2[c];
         } else {
             // m+ = soft(z + gamma g, gamma lambda); z+ = m+ + beta (m+ - m)
+            float gam = fa.gamma, th = fa.thresh;
+            if (fa.cube_gt) {
+                const float2 gt = __ldg(fa.cube_gt + cg.cube);
+                gam = gt.x;
+                th = gt.y;
+            }
             float *__restrict__ mp = fa.m + o;
             float *__restrict__ zp = fa.z + o;
             float mo[2 * P], zo[2 * P];
@@ -268,7 +269,7 @@ c2r_kernel(const float2 *__restrict__ in, float *__restrict__ out,
 #pragma unroll
             for (int c = 0; c < 2 * P; ++c) {
                 if (c >= nc) break;
-                const float mn = soft_threshold(fmaf(fa.gamma, g2[c], zo[c]), fa.thresh);
+                const float mn = soft_threshold(fmaf(gam, g2[c], zo[c]), th);
                 mp[c] = mn;
                 zp[c] = fmaf(fa.beta, mn - mo[c], mn);
             }

@@ -30,10 +30,11 @@ def _geom(nt, dt, ntau, nq, q0, dq, ntheta, hx, hy, keep):
                         hy.ctypes.data_as(dp))
 
 
-def _opts(interp="keys", spread_width=0, theta_group=0, ngather=1, sigma_t=0.0, fmax=0.0):
+def _opts(interp="keys", spread_width=0, theta_group=0, ngather=1, sigma_t=0.0, fmax=0.0,
+          time_pairs=0, autotune=False):
     kind = {"keys": L.AAHRT_INTERP_KEYS, "linear": L.AAHRT_INTERP_LINEAR}[interp]
     return L.aahrt_opts(kind, int(spread_width), int(theta_group), int(ngather),
-                        float(sigma_t), float(fmax))
+                        float(sigma_t), float(fmax), int(time_pairs), int(bool(autotune)))
 
 
 class AahrtPlan:
@@ -41,14 +42,15 @@ class AahrtPlan:
 
     def __init__(self, nt, dt, ntau, nq, q0, dq, ntheta, hx, hy, *, interp="keys",
                  spread_width=0, theta_group=0, ngather=1, sigma_t=0.0, fmax=0.0,
-                 _handle=None, _shapes=None):
+                 time_pairs=0, autotune=False, _handle=None, _shapes=None):
         if _handle is not None:
             self.handle = _handle
         else:
             keep = []
             g = _geom(nt, dt, ntau, nq, q0, dq, ntheta, hx, hy, keep)
             self.handle = L.aahrt_plan_create(
-                g, _opts(interp, spread_width, theta_group, ngather, sigma_t, fmax))
+                g, _opts(interp, spread_width, theta_group, ngather, sigma_t, fmax,
+                         time_pairs, autotune))
         self.info = L.aahrt_plan_query(self.handle)
         self.nt, self.ntau, self.nq, self.ntheta = nt, ntau, nq, ntheta
         self.device = torch.device("cuda", torch.cuda.current_device())
@@ -59,12 +61,13 @@ class AahrtPlan:
 
     @classmethod
     def batched(cls, gathers: Sequence, interp="keys", spread_width=0, theta_group=0,
-                sigma_t=0.0, fmax=0.0):
+                sigma_t=0.0, fmax=0.0, time_pairs=0, autotune=False):
         keep = []
         geoms = [_geom(g.nt, g.dt, g.ntau, g.nq, g.q0, g.dq, g.ntheta, g.hx, g.hy, keep)
                  for g in gathers]
         h = L.aahrt_plan_create_batched(
-            geoms, _opts(interp, spread_width, theta_group, 1, sigma_t, fmax))
+            geoms, _opts(interp, spread_width, theta_group, 1, sigma_t, fmax, time_pairs,
+                         autotune))
         g0 = gathers[0]
         return cls(g0.nt, g0.dt, g0.ntau, g0.nq, g0.q0, g0.dq, g0.ntheta, None, None,
                    _handle=h)
@@ -107,17 +110,49 @@ class AahrtPlan:
     def sparse_solve(self, d: torch.Tensor, lam: float, iters: int,
                      m: Optional[torch.Tensor] = None, *, ista=False, gamma=0.0,
                      lambda_rel=0.0, power_iters=0, warm_start=False, use_graph=True,
-                     want_info=True, stream=None):
-        """Sparse transform (eq. cost1) by ISTA/FISTA iterations (eq. ISTA)."""
+                     want_info=True, per_cube=False, cube_gamma=None, cube_lambda=None,
+                     stream=None):
+        """Sparse transform (eq. cost1) by ISTA/FISTA iterations (eq. ISTA).
+        With per_cube, every cube (gather) is solved with its own step and
+        threshold; cube_gamma / cube_lambda (float64 numpy arrays of ncube, or
+        None) give them (entries <= 0 of cube_gamma are estimated) and
+        receive the values used."""
         self._check(d, self.data_len, "d")
         if m is None:
             m = torch.zeros(self.model_len, device=d.device, dtype=torch.float32)
         self._check(m, self.model_len, "m")
+        dp = ctypes.POINTER(ctypes.c_double)
+        arrs = []
+        for a in (cube_gamma, cube_lambda):
+            if a is None:
+                arrs.append(None)
+                continue
+            if (not isinstance(a, np.ndarray) or a.dtype != np.float64 or
+                    a.shape != (int(self.info.ncube),) or not a.flags.c_contiguous):
+                raise ValueError("cube_gamma / cube_lambda must be contiguous float64 arrays "
+                                 "of ncube")
+            arrs.append(a.ctypes.data_as(dp))
         o = L.aahrt_solve_opts(int(bool(ista)), int(bool(warm_start)), int(power_iters),
-                               int(bool(use_graph)), float(gamma), float(lambda_rel))
+                               int(bool(use_graph)), float(gamma), float(lambda_rel),
+                               int(bool(per_cube)), arrs[0], arrs[1])
         info = L.aahrt_sparse_solve(self.handle, d.data_ptr(), float(lam), int(iters),
                                     m.data_ptr(), o, want_info, _stream_ptr(stream))
         return m, info
+
+    def fista_vjp(self, d: torch.Tensor, m_bar: torch.Tensor, lam: float, gamma: float,
+                  iters: int, *, ista=False, checkpoint=0, want_m=True, stream=None):
+        """(m^iters, d_bar) of the unrolled solve: d_bar = (dm/dd)^T m_bar
+        (see aahrt_fista_vjp)."""
+        self._check(d, self.data_len, "d")
+        self._check(m_bar, self.model_len, "m_bar")
+        d_bar = torch.empty(self.data_len, device=d.device, dtype=torch.float32)
+        m_out = (torch.empty(self.model_len, device=d.device, dtype=torch.float32)
+                 if want_m else None)
+        L.aahrt_fista_vjp(self.handle, d.data_ptr(), m_bar.data_ptr(), float(lam),
+                          float(gamma), int(iters), ista, int(checkpoint),
+                          m_out.data_ptr() if m_out is not None else 0, d_bar.data_ptr(),
+                          _stream_ptr(stream))
+        return m_out, d_bar
 
     def apply_stage(self, stage: int, x: torch.Tensor, out: Optional[torch.Tensor] = None,
                     stream=None):

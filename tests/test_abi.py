@@ -123,3 +123,34 @@ def test_package_import_does_not_load_cuda():
             continue
     mod = importlib.import_module("paper_2505_00387_gb300.synthetic")
     assert hasattr(mod, "config0")
+
+
+def test_ctypes_structs_match_the_header(tmp_path):
+    """sizeof and every field offset of the ABI structs, as the C compiler
+    lays them out from include/aahrt.h, equal the ctypes mirrors."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"aahrt_geom": L.aahrt_geom, "aahrt_opts": L.aahrt_opts,
+               "aahrt_plan_info": L.aahrt_plan_info, "aahrt_solve_opts": L.aahrt_solve_opts,
+               "aahrt_solve_info": L.aahrt_solve_info}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "aahrt.h"',
+             "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    got = dict(line.rsplit(" ", 1) for line in out.strip().splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert int(got[f"{name}.{f}"]) == getattr(cls, f).offset, f"{name}.{f}"
