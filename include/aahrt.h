@@ -71,6 +71,20 @@ extern "C" {
 #define AAHRT_INTERP_KEYS 0        /* Keys cubic convolution, a = -1/2 (default) */
 #define AAHRT_INTERP_LINEAR 1      /* linear interpolation */
 
+/* Slice-step arithmetic.
+ * AAHRT_PRECISION_FP32: the non-uniform DFT along q by an exponential-of-
+ *   semicircle spreading kernel on an oversampled q grid, FP32 on the CUDA
+ *   cores (about 2e-6 relative to the exact operator).
+ * AAHRT_PRECISION_SPLIT_BF16: for ngather gathers on one geometry (plans of
+ *   aahrt_plan_create; ngather <= 64, nq <= 256), the slice step of every bin
+ *   and azimuth slice is a direct complex contraction over q (traces) with
+ *   the exact phases exp(-+2 pi i f_k q_l r^2), run on the tensor cores with
+ *   every FP32 operand split into two bf16 parts (three products, FP32
+ *   accumulation; about 1e-5 relative).  Its model and data buffers hold the
+ *   gathers fastest: m[tau][q][theta][g], d[t][trace][g]. */
+#define AAHRT_PRECISION_FP32 0
+#define AAHRT_PRECISION_SPLIT_BF16 1
+
 typedef struct aahrt_plan aahrt_plan;
 
 /* Axes and trace geometry of one CMP cube.  hx, hy: host arrays of ntr
@@ -106,6 +120,7 @@ typedef struct {
     int autotune;       /* 1: pick spread_width, theta_group and time_pairs
                            at plan creation (see aahrt_plan_create); fields
                            set explicitly above are kept */
+    int precision;      /* AAHRT_PRECISION_FP32 (0) or AAHRT_PRECISION_SPLIT_BF16 */
 } aahrt_opts;
 
 /* What a plan chose (filled by aahrt_plan_query). */
@@ -129,6 +144,7 @@ typedef struct {
     int time_pairs;          /* column pairs per time-kernel block */
     int autotuned;           /* 1 if the autotuner chose the tiles above */
     double tune_ms;          /* autotuner: best forward+adjoint time of its trial batch */
+    int precision;           /* AAHRT_PRECISION_* of the slice step */
 } aahrt_plan_info;
 
 /* Create a plan on the current CUDA device: validates the geometry,
@@ -286,6 +302,12 @@ int aahrt_plan_stage_times(aahrt_plan *plan, double *times_ms,
  * on the GPU race on it and must be serialised. */
 #define AAHRT_NOALLOC_SCRATCH_BYTES (16u << 20)
 int aahrt_forward_noalloc(aahrt_plan *plan, const float *m, float *d, void *stream);
+
+/* Synchronises the plan's device and reports device-side failures of its
+ * kernels since the last call: AAHRT_ERR_TIMEOUT if a tensor-core kernel
+ * gave up waiting for its matrix unit (its output is then incomplete), else
+ * AAHRT_OK.  The flag is cleared. */
+int aahrt_plan_status(aahrt_plan *plan);
 
 const char *aahrt_status_string(int status);
 const char *aahrt_last_error(void);

@@ -20,6 +20,8 @@ AAHRT_ERR_TIMEOUT = -5
 AAHRT_ERR_NONFINITE = -6
 AAHRT_INTERP_KEYS = 0
 AAHRT_INTERP_LINEAR = 1
+AAHRT_PRECISION_FP32 = 0
+AAHRT_PRECISION_SPLIT_BF16 = 1
 AAHRT_NSTAGES = 7
 STAGE_NAMES = ("stretch_fft", "slice_fwd", "ifft_unstretch", "unstretchT_fft",
                "slice_adj", "ifft_stretchT", "solver_updates")
@@ -34,7 +36,7 @@ class aahrt_geom(ctypes.Structure):
 class aahrt_opts(ctypes.Structure):
     _fields_ = [("interp_kind", c_int), ("spread_width", c_int), ("theta_group", c_int),
                 ("ngather", c_int), ("sigma_t", c_double), ("fmax", c_double),
-                ("time_pairs", c_int), ("autotune", c_int)]
+                ("time_pairs", c_int), ("autotune", c_int), ("precision", c_int)]
 
 
 class aahrt_plan_info(ctypes.Structure):
@@ -44,7 +46,7 @@ class aahrt_plan_info(ctypes.Structure):
                 ("model_len", c_longlong), ("data_len", c_longlong),
                 ("xspec_len", c_longlong), ("yspec_len", c_longlong),
                 ("workspace_bytes", c_longlong), ("time_pairs", c_int), ("autotuned", c_int),
-                ("tune_ms", c_double)]
+                ("tune_ms", c_double), ("precision", c_int)]
 
 
 class aahrt_solve_opts(ctypes.Structure):
@@ -87,6 +89,7 @@ _SIGS = {
                                       POINTER(c_double)]),
     "aahrt_plan_set_profiling": (c_int, [c_void_p, c_int]),
     "aahrt_plan_stage_times": (c_int, [c_void_p, POINTER(c_double), POINTER(c_longlong)]),
+    "aahrt_plan_status": (c_int, [c_void_p]),
     "aahrt_status_string": (ctypes.c_char_p, [c_int]),
     "aahrt_last_error": (ctypes.c_char_p, []),
 }
@@ -200,6 +203,10 @@ def aahrt_plan_stage_times(h):
     n = (c_longlong * AAHRT_NSTAGES)()
     check(load().aahrt_plan_stage_times(h, t, n), "aahrt_plan_stage_times")
     return list(t), list(n)
+
+
+def aahrt_plan_status(h):
+    check(load().aahrt_plan_status(h), "aahrt_plan_status")
 
 
 def aahrt_status_string(status: int) -> str:

@@ -776,6 +776,23 @@ int aahrt_plan_stage_times(aahrt_plan *plan, double *times_ms, long long *launch
     return AAHRT_OK;
 }
 
+int aahrt_plan_status(aahrt_plan *plan) {
+    if (!plan) return set_error(AAHRT_ERR_INVALID_ARG, "plan is NULL");
+    Plan &p = *plan->p;
+    DeviceGuard g(p.device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e) return cuda_fail(e, "synchronise");
+    int flag = 0;
+    if ((e = cudaMemcpy(&flag, p.counters + kTcErrSlot, sizeof flag, cudaMemcpyDeviceToHost)))
+        return cuda_fail(e, "read status");
+    if (flag) {
+        cudaMemset(p.counters + kTcErrSlot, 0, sizeof(int));
+        return set_error(AAHRT_ERR_TIMEOUT, "a tensor-core kernel timed out waiting for its "
+                         "matrix operations");
+    }
+    return AAHRT_OK;
+}
+
 const char *aahrt_status_string(int status) {
     switch (status) {
         case AAHRT_OK: return "success";

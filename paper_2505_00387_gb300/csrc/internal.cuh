@@ -148,6 +148,11 @@ struct Plan {
     float2 *cube_gt = nullptr;     // per-cube (gamma, gamma*lambda) of a per-cube solve
     double *cube_acc = nullptr;    // per-cube FP64 accumulators [slot][ncube]
     long long *dseg = nullptr;     // data offsets of the cubes (ncube + 1 entries)
+    // tensor-core direct contraction (precision 1): gathers stored fastest
+    int precision = 0;
+    int tc_gp = 0;                 // gathers padded to a multiple of 8
+    int4 *tc_tiles = nullptr;      // forward row tiles {slice, first, end, 0}
+    int tc_ntiles = 0;
     // tiles
     bool autotuned = false;
     double tune_ms = 0;
@@ -188,6 +193,11 @@ cudaError_t launch_c2r(Plan &p, bool model_side, const float2 *in, float *out,
                        bool blocked = false);
 cudaError_t launch_slice(Plan &p, bool adjoint, const float2 *in, float2 *out,
                          cudaStream_t st, int *counter = nullptr);
+cudaError_t launch_slice_tc(Plan &p, bool adjoint, const float2 *in, float2 *out,
+                            cudaStream_t st, int *counter);
+cudaError_t configure_tc_kernels(Plan &p, int num_sms, int max_smem);
+// device error flag of the tensor-core kernels (a timed-out wait), in Plan::counters
+constexpr int kTcErrSlot = 8;
 
 // profiling brackets around a stage launch
 void prof_begin(Plan &p, int stage, cudaStream_t st);

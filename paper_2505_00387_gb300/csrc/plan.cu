@@ -183,7 +183,7 @@ void free_plan(Plan *p) {
                     p->cg_model, p->cg_data, p->cg_model_blk, p->cg_data_blk, p->posS,
                     p->posU, p->rngST, p->rngUT, p->X, p->Y, p->z, p->r, p->v, p->scal,
                     p->stage_m, p->stage_d, p->zb, p->mb, p->rb, p->db, p->vjp_ws,
-                    p->cube_gt, p->cube_acc, p->dseg};
+                    p->cube_gt, p->cube_acc, p->dseg, p->tc_tiles};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     cudaSetDevice(cur);
@@ -245,6 +245,21 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
     if (opts.time_pairs != 0 && opts.time_pairs != 1 && opts.time_pairs != 2 &&
         opts.time_pairs != 4 && opts.time_pairs != 8)
         return set_error(AAHRT_ERR_INVALID_ARG, "time_pairs must be 0, 1, 2, 4 or 8");
+    if (opts.precision != AAHRT_PRECISION_FP32 && opts.precision != AAHRT_PRECISION_SPLIT_BF16)
+        return set_error(AAHRT_ERR_INVALID_ARG, "precision must be 0 or 1");
+    // the tensor-core contraction serves gathers on one geometry, stored
+    // gather-fastest: internally one cube whose columns are (column, gather)
+    const bool tc = opts.precision == AAHRT_PRECISION_SPLIT_BF16;
+    const int G_tc = tc ? ncube : 1;
+    if (tc) {
+        if (ndist != 1)
+            return set_error(AAHRT_ERR_UNSUPPORTED,
+                             "the tensor-core contraction needs gathers on one geometry");
+        if (G_tc > 64 || g0.nq > 256)
+            return set_error(AAHRT_ERR_UNSUPPORTED,
+                             "the tensor-core contraction supports ngather <= 64, nq <= 256");
+        ncube = 1;
+    }
 
     Plan *p = new Plan();
     cudaGetDevice(&p->device);
@@ -259,7 +274,9 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
     p->sigma_t = opts.sigma_t > 0.0 ? opts.sigma_t : 2.0;
     p->fmax = opts.fmax;
     p->ncube = ncube;
-    p->ngather = ndist == 1 ? ncube : 1;
+    p->ngather = tc ? G_tc : (ndist == 1 ? ncube : 1);
+    p->precision = opts.precision;
+    p->tc_gp = tc ? (G_tc + 7) / 8 * 8 : 0;
 
     // ---------------------------------------------------- stretched time
     double r2max = 0.0;
@@ -355,10 +372,10 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
     p->ntr_total = acc_tr;
     const long long C = (long long)p->nq * p->ntheta;
     p->cols_model = C;
-    p->model_len = (long long)ncube * p->ntau * C;
-    p->data_len = acc_tr * p->nt;
-    p->x_len = (long long)ncube * p->nbins * C;
-    p->y_len = acc_tr * p->nbins;
+    p->model_len = (long long)ncube * p->ntau * C * G_tc;
+    p->data_len = acc_tr * p->nt * G_tc;
+    p->x_len = (long long)ncube * p->nbins * C * G_tc;
+    p->y_len = acc_tr * p->nbins * G_tc;
 
     std::vector<SliceGroup> groups;
     for (int c = 0; c < ncube; ++c) {
@@ -394,7 +411,15 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
     // ------------------------------------------------- column groups
     const int cpg = 2 * p->pairs;
     std::vector<ColGroup> cgm, cgd;
-    for (int c = 0; c < ncube; ++c)
+    if (tc) {
+        // columns (q, theta, gather) and (trace, gather), gather fastest
+        const long long Ct = C * G_tc, Dt = (long long)p->ntr[0] * G_tc;
+        for (long long c0 = 0; c0 < Ct; c0 += cpg)
+            cgm.push_back(ColGroup{c0, c0, (int)Ct, (int)Ct, (int)std::min<long long>(cpg, Ct - c0), 0});
+        for (long long h0 = 0; h0 < Dt; h0 += cpg)
+            cgd.push_back(ColGroup{h0, h0, (int)Dt, (int)Dt, (int)std::min<long long>(cpg, Dt - h0), 0});
+    }
+    for (int c = 0; c < (tc ? 0 : ncube); ++c)
         for (long long c0 = 0; c0 < C; c0 += cpg) {
             ColGroup q;
             q.real_off = (long long)c * p->ntau * C + c0;
@@ -405,7 +430,7 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
             q.cube = c;
             cgm.push_back(q);
         }
-    for (int c = 0; c < ncube; ++c)
+    for (int c = 0; c < (tc ? 0 : ncube); ++c)
         for (int h0 = 0; h0 < p->ntr[c]; h0 += cpg) {
             ColGroup q;
             q.real_off = p->data_off[c] + h0;
@@ -533,7 +558,17 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
     // shared by every plan of the process: raise it to the device maximum once
     // so no plan lowers it under another.
     AAHRT_TRY(set_time_kernel_attrs(p->lp, p->interp, max_smem), "kernel attributes");
-    AAHRT_TRY(configure_slice_kernels(*p, num_sms, max_smem), "slice kernel configuration");
+    if (tc) {
+        std::vector<int4> tiles;
+        for (int j = 0; j < p->ntheta; ++j)
+            for (int t0 = ss_all[j]; t0 < ss_all[j + 1]; t0 += 128)
+                tiles.push_back(make_int4(j, t0, std::min(t0 + 128, ss_all[j + 1]), 0));
+        p->tc_ntiles = (int)tiles.size();
+        AAHRT_TRY(upload(&p->tc_tiles, tiles), "upload row tiles");
+        AAHRT_TRY(configure_tc_kernels(*p, num_sms, max_smem), "tensor-core kernel configuration");
+    } else {
+        AAHRT_TRY(configure_slice_kernels(*p, num_sms, max_smem), "slice kernel configuration");
+    }
 #undef AAHRT_TRY
     *out = p;
     return AAHRT_OK;
@@ -560,6 +595,7 @@ void plan_info(const Plan &p, aahrt_plan_info *info) {
     info->time_pairs = p.pairs;
     info->autotuned = p.autotuned ? 1 : 0;
     info->tune_ms = p.tune_ms;
+    info->precision = p.precision;
 }
 
 // ----------------------------------------------------------- profiling

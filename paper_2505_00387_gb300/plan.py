@@ -30,11 +30,15 @@ def _geom(nt, dt, ntau, nq, q0, dq, ntheta, hx, hy, keep):
                         hy.ctypes.data_as(dp))
 
 
+PRECISIONS = {"fp32": L.AAHRT_PRECISION_FP32, "split_bf16": L.AAHRT_PRECISION_SPLIT_BF16}
+
+
 def _opts(interp="keys", spread_width=0, theta_group=0, ngather=1, sigma_t=0.0, fmax=0.0,
-          time_pairs=0, autotune=False):
+          time_pairs=0, autotune=False, precision="fp32"):
     kind = {"keys": L.AAHRT_INTERP_KEYS, "linear": L.AAHRT_INTERP_LINEAR}[interp]
     return L.aahrt_opts(kind, int(spread_width), int(theta_group), int(ngather),
-                        float(sigma_t), float(fmax), int(time_pairs), int(bool(autotune)))
+                        float(sigma_t), float(fmax), int(time_pairs), int(bool(autotune)),
+                        PRECISIONS[precision])
 
 
 class AahrtPlan:
@@ -42,7 +46,8 @@ class AahrtPlan:
 
     def __init__(self, nt, dt, ntau, nq, q0, dq, ntheta, hx, hy, *, interp="keys",
                  spread_width=0, theta_group=0, ngather=1, sigma_t=0.0, fmax=0.0,
-                 time_pairs=0, autotune=False, _handle=None, _shapes=None):
+                 time_pairs=0, autotune=False, precision="fp32", _handle=None,
+                 _shapes=None):
         if _handle is not None:
             self.handle = _handle
         else:
@@ -50,7 +55,7 @@ class AahrtPlan:
             g = _geom(nt, dt, ntau, nq, q0, dq, ntheta, hx, hy, keep)
             self.handle = L.aahrt_plan_create(
                 g, _opts(interp, spread_width, theta_group, ngather, sigma_t, fmax,
-                         time_pairs, autotune))
+                         time_pairs, autotune, precision))
         self.info = L.aahrt_plan_query(self.handle)
         self.nt, self.ntau, self.nq, self.ntheta = nt, ntau, nq, ntheta
         self.device = torch.device("cuda", torch.cuda.current_device())
@@ -171,6 +176,11 @@ class AahrtPlan:
         L.aahrt_apply_stage(self.handle, stage, x.data_ptr(), out.data_ptr(),
                             _stream_ptr(stream))
         return out
+
+    def status(self):
+        """Synchronise; raise AahrtError if a kernel reported a device-side
+        timeout since the last check."""
+        L.aahrt_plan_status(self.handle)
 
     def set_profiling(self, on: bool):
         L.aahrt_plan_set_profiling(self.handle, on)
