@@ -197,7 +197,11 @@ int aahrt_adjoint(aahrt_plan *plan, const float *d, float *m, void *stream);
  * F: DFT along stretched time (Alg. 1 step 2); H: band-limited Hermitian
  * synthesis x_n = Re X_0 + 2 Re sum_{k>=1} X_k e^{+2 pi i k n/nfft} (so
  * H/nfft is the paper's F1^{-1}, step 4); S, U: the stretch and its undoing
- * (steps 1 and 5).  forward = 2 o 1 o 0, adjoint = 5 o 4 o 3. */
+ * (steps 1 and 5).  forward = 2 o 1 o 0, adjoint = 5 o 4 o 3.
+ * Plans of AAHRT_PRECISION_SPLIT_BF16 keep their spectra slice-major with
+ * the gathers fastest: X[theta][k][q][g] and Y[j][k][i][g], where block j
+ * holds the traces whose first azimuth slice is j (i = rank of the trace
+ * among them, in input order). */
 int aahrt_apply_stage(aahrt_plan *plan, int stage, const void *in, void *out,
                       void *stream);
 

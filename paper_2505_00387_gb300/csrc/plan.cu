@@ -412,12 +412,33 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
     const int cpg = 2 * p->pairs;
     std::vector<ColGroup> cgm, cgd;
     if (tc) {
-        // columns (q, theta, gather) and (trace, gather), gather fastest
-        const long long Ct = C * G_tc, Dt = (long long)p->ntr[0] * G_tc;
-        for (long long c0 = 0; c0 < Ct; c0 += cpg)
-            cgm.push_back(ColGroup{c0, c0, (int)Ct, (int)Ct, (int)std::min<long long>(cpg, Ct - c0), 0});
-        for (long long h0 = 0; h0 < Dt; h0 += cpg)
-            cgd.push_back(ColGroup{h0, h0, (int)Dt, (int)Dt, (int)std::min<long long>(cpg, Dt - h0), 0});
+        // Real columns (q, theta, gather) and (trace, gather), gather fastest;
+        // spectra slice-major, X[j][k][l][g] and Y[j][k][i][g] (i = the trace's
+        // rank inside slice j), so each (bin, slice) block is contiguous.  A
+        // column group never straddles two (q, theta) or two traces.
+        const int G = G_tc, J = p->ntheta, nq = p->nq;
+        const long long nb = p->nbins;
+        for (int l = 0; l < nq; ++l)
+            for (int j = 0; j < J; ++j)
+                for (int g0 = 0; g0 < G; g0 += cpg)
+                    cgm.push_back(ColGroup{((long long)l * J + j) * G + g0,
+                                           ((long long)j * nb * nq + l) * G + g0,
+                                           (int)(C * G), nq * G, std::min(cpg, G - g0), 0});
+        const CubeGeo &cg0 = cg[0];
+        std::vector<int> rank(p->ntr[0]), slice(p->ntr[0]);
+        for (int j = 0; j < J; ++j)
+            for (int t = cg0.start[j]; t < cg0.start[j + 1]; ++t) {
+                rank[cg0.sorted[t].col] = t - cg0.start[j];
+                slice[cg0.sorted[t].col] = j;
+            }
+        for (int h = 0; h < p->ntr[0]; ++h) {
+            const int j = slice[h];
+            const int cnt = cg0.start[j + 1] - cg0.start[j];
+            for (int g0 = 0; g0 < G; g0 += cpg)
+                cgd.push_back(ColGroup{(long long)h * G + g0,
+                                       (nb * cg0.start[j] + rank[h]) * G + g0,
+                                       p->ntr[0] * G, cnt * G, std::min(cpg, G - g0), 0});
+        }
     }
     for (int c = 0; c < (tc ? 0 : ncube); ++c)
         for (long long c0 = 0; c0 < C; c0 += cpg) {

@@ -2,8 +2,10 @@
 // for gathers that share one geometry (Algorithm 1 step 3 / its transpose,
 // eqs. Inv_op, inv_GFST, theta factors of eq. thli).
 //
-// With G gathers stored gather-fastest (X[k][l][j][g], Y[k][trace][g]), the
-// slice step of bin k for the traces h whose first azimuth slice is j is
+// With G gathers stored gather-fastest in slice-major spectra
+// (X[j][k][l][g], Y[j][k][i][g] with i the trace's rank inside slice j, so
+// every (bin, slice) block is contiguous), the slice step of bin k for the
+// traces h whose first azimuth slice is j is
 //   Y[h][g] = scale * sum_s w_s(h) sum_l E[h][l] X[l][j_s][g],
 //   E[h][l] = exp(-2 pi i f_k q_l r_h^2),  j_0 = j, j_1 = j + 1 (mod ntheta),
 // a complex GEMM (traces x q) * (q x 2G) per (k, j); the adjoint of slice j,
@@ -20,7 +22,7 @@
 //   A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi   (FP32 accumulation in TMEM).
 // The phase arguments are range-reduced exactly in 64-bit fixed point.
 //
-// One CTA per SM (persistent, items from an atomic counter); all 8 warps
+// One CTA per SM (persistent, items from an atomic counter); all 16 warps
 // build the bf16 operand tiles of a K chunk (64 K-elements) in shared memory
 // (128-byte swizzled K-major layout) while the tensor core works on the
 // previous chunk (two stages, mbarrier-tracked tcgen05.commit); thread 0
@@ -34,7 +36,7 @@ namespace aahrt {
 
 using namespace tc;
 
-constexpr int kTcThreads = 256;
+constexpr int kTcThreads = 512;
 constexpr uint32_t kTileA = 128u * 128u;     // one 128-row x 64-element bf16 tile
 constexpr uint32_t kTcWait = 1u << 24;       // mbarrier polls before giving up
 constexpr int kTcMaxGp = 64;
@@ -54,23 +56,22 @@ __device__ __forceinline__ unsigned char *align1024(unsigned char *p) {
     return (unsigned char *)(((uintptr_t)p + 1023) & ~(uintptr_t)1023);
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
-    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a)) |
-           ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
+// (a, b) -> bf16x2 hi parts and bf16x2 lo parts (a - hi_a, b - hi_b); one
+// packed conversion each way
+__device__ __forceinline__ void split2(float a, float b, uint32_t *hi, uint32_t *lo) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+    *hi = *reinterpret_cast<const uint32_t *>(&h);
+    *lo = *reinterpret_cast<const uint32_t *>(&l);
 }
 
 // 8 floats -> hi and lo bf16 chunks (16 bytes each)
 __device__ __forceinline__ void split8(const float *v, uint4 *hi, uint4 *lo) {
-    float h[8], l[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        h[i] = __bfloat162float(__float2bfloat16_rn(v[i]));
-        l[i] = v[i] - h[i];
-    }
-    *hi = make_uint4(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]), pack_bf16(h[4], h[5]),
-                     pack_bf16(h[6], h[7]));
-    *lo = make_uint4(pack_bf16(l[0], l[1]), pack_bf16(l[2], l[3]), pack_bf16(l[4], l[5]),
-                     pack_bf16(l[6], l[7]));
+    split2(v[0], v[1], &hi->x, &lo->x);
+    split2(v[2], v[3], &hi->y, &lo->y);
+    split2(v[4], v[5], &hi->z, &lo->z);
+    split2(v[6], v[7], &hi->w, &lo->w);
 }
 
 // 16-byte chunk c (K-elements 8c .. 8c+7) of row r of a swizzled tile
@@ -80,9 +81,9 @@ __device__ __forceinline__ void st_chunk(unsigned char *tile, int r, int c, uint
 
 // exp(sgn * 2 pi i x), x a fixed-point fraction of a cycle (2^-64 units)
 __device__ __forceinline__ float2 cis_fixed(unsigned long long x, float sgn) {
-    const float f = (float)(int)(unsigned)(x >> 32) * 2.3283064365386963e-10f;
+    const float f = (float)(int)(unsigned)(x >> 32) * 2.3283064365386963e-10f;   // [-1/2, 1/2)
     float s, c;
-    sincospif(2.0f * f, &s, &c);
+    __sincosf(6.28318530717958647692f * f, &s, &c);     // |angle| <= pi
     return make_float2(c, sgn * s);
 }
 
@@ -194,7 +195,9 @@ slice_fwd_tc_kernel(const TcArgs a, const float2 *__restrict__ X, float2 *__rest
         const int4 tile = a.tiles[item - (long long)k * a.ntiles];
         const int j = tile.x, t0 = tile.y, t1 = tile.z;
         const int jn = j + 1 == J ? 0 : j + 1;
-        const float2 *Xk = X + (long long)k * a.nq * J * a.G;
+        const long long blk = (long long)a.nq * a.G;          // one (bin, slice) block of X
+        const float2 *Xj = X + ((long long)j * a.nbins + k) * blk;
+        const float2 *Xn = X + ((long long)jn * a.nbins + k) * blk;
 
         for (int c = 0; c < nch; ++c) {
             const int b = c & 1;
@@ -226,14 +229,14 @@ slice_fwd_tc_kernel(const TcArgs a, const float2 *__restrict__ X, float2 *__rest
                 const int g = u % Gp;
                 const int rest = u / Gp;
                 const int sl = rest & 1, lb = rest >> 1;
-                const int js = sl ? jn : j;
+                const float2 *Xs = sl ? Xn : Xj;
                 const int l0 = 32 * c + 8 * lb;
                 float vr[16], vi[16];
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
                     const int l = l0 + i;
                     float2 x = make_float2(0.f, 0.f);
-                    if (l < a.nq && g < a.G) x = __ldg(Xk + ((long long)l * J + js) * a.G + g);
+                    if (l < a.nq && g < a.G) x = __ldg(Xs + (long long)l * a.G + g);
                     vr[2 * i] = x.x;
                     vr[2 * i + 1] = -x.y;
                     vi[2 * i] = x.y;
@@ -276,15 +279,16 @@ slice_fwd_tc_kernel(const TcArgs a, const float2 *__restrict__ X, float2 *__rest
         if (s.failed) continue;
 
         // epilogue: Y[h][g] = scale (w0 P[h][g, j] + w1 P[h][g, j+1])
-        const int q = warp & 3, half = warp >> 2;
+        const int q = warp & 3, quarter = warp >> 2;
         const int r = 32 * q + lane;
         const int t = t0 + r;
         const bool valid = t < t1;
         TraceGeo tr{};
         if (valid) tr = a.geo[t];
         const uint32_t lanebase = s.tm + ((uint32_t)(32 * q) << 16);
-        float2 *Yrow = Y + ((long long)k * a.ntr + (valid ? tr.col : 0)) * a.G;
-        for (int gb = 16 * half; gb < Gp; gb += 32) {
+        const int s0 = a.ss[j], cnt = a.ss[j + 1] - s0;
+        float2 *Yrow = Y + ((long long)a.nbins * s0 + (long long)k * cnt + (valid ? t - s0 : 0)) * a.G;
+        for (int gb = 16 * quarter; gb < Gp; gb += 64) {
             float re0[16], re1[16], im0[16], im1[16];
             tmem_ld16(lanebase + gb, re0);
             tmem_ld16(lanebase + Gp + gb, re1);
@@ -332,7 +336,9 @@ slice_adj_tc_kernel(const TcArgs a, const float2 *__restrict__ Yh, float2 *__res
         const int b0 = a.ss[jm], n2 = a.ss[jm + 1] - b0;    // weight w1
         const int ntot = n1 + n2;
         const int nch = (ntot + 31) >> 5;
-        const float2 *Yk = Yh + (long long)k * a.ntr * a.G;
+        // slice blocks of Y^: slice j (weight w0) and slice j - 1 (weight w1)
+        const float2 *Ya = Yh + ((long long)a.nbins * a0 + (long long)k * n1) * a.G;
+        const float2 *Yb = Yh + ((long long)a.nbins * b0 + (long long)k * n2) * a.G;
 
         for (int c = 0; c < nch; ++c) {
             const int b = c & 1;
@@ -364,15 +370,11 @@ slice_adj_tc_kernel(const TcArgs a, const float2 *__restrict__ Yh, float2 *__res
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         const int r = (l0 & 127) + i;
-                        const __nv_bfloat16 rh = __float2bfloat16_rn(e[i].x);
-                        const __nv_bfloat16 ih = __float2bfloat16_rn(e[i].y);
-                        const float rl = e[i].x - __bfloat162float(rh);
-                        const float il = e[i].y - __bfloat162float(ih);
+                        uint32_t h, lo;
+                        split2(e[i].x, e[i].y, &h, &lo);
                         const uint32_t off = sw128_offset((uint32_t)r, (uint32_t)(2 * hh));
-                        *reinterpret_cast<uint32_t *>(ahi + off) =
-                            (uint32_t)__bfloat16_as_ushort(rh) |
-                            ((uint32_t)__bfloat16_as_ushort(ih) << 16);
-                        *reinterpret_cast<uint32_t *>(alo + off) = pack_bf16(rl, il);
+                        *reinterpret_cast<uint32_t *>(ahi + off) = h;
+                        *reinterpret_cast<uint32_t *>(alo + off) = lo;
                     }
                 }
             }
@@ -384,10 +386,9 @@ slice_adj_tc_kernel(const TcArgs a, const float2 *__restrict__ Yh, float2 *__res
                 for (int i = 0; i < 8; ++i) {
                     const int p = 32 * c + 8 * tb + i;
                     float2 y = make_float2(0.f, 0.f);
-                    if (p < ntot && g < a.G) {
-                        const int t = p < n1 ? a0 + p : b0 + (p - n1);
-                        y = __ldg(Yk + (long long)a.geo[t].col * a.G + g);
-                    }
+                    if (p < ntot && g < a.G)
+                        y = __ldg(p < n1 ? Ya + (long long)p * a.G + g
+                                         : Yb + (long long)(p - n1) * a.G + g);
                     vr[2 * i] = y.x;
                     vr[2 * i + 1] = -y.y;
                     vi[2 * i] = y.y;
@@ -435,12 +436,12 @@ slice_adj_tc_kernel(const TcArgs a, const float2 *__restrict__ Yh, float2 *__res
         if (s.failed) continue;
 
         // epilogue: X^[l][j][g] = scale * accumulator (zero without traces)
-        const int q = warp & 3, mt = warp >> 2;
+        const int q = warp & 3, mt = (warp >> 2) & 1, half = warp >> 3;
         if (mt < nmt) {
             const int l = 128 * mt + 32 * q + lane;
             const uint32_t base = s.tm + ((uint32_t)(32 * q) << 16) + (uint32_t)(mt * N);
-            float2 *Xrow = Xh + (((long long)k * a.nq + (l < a.nq ? l : 0)) * J + j) * a.G;
-            for (int gb = 0; gb < Gp; gb += 16) {
+            float2 *Xrow = Xh + (((long long)j * a.nbins + k) * a.nq + (l < a.nq ? l : 0)) * a.G;
+            for (int gb = 16 * half; gb < Gp; gb += 32) {
                 float re[16], im[16];
                 if (nch > 0) {
                     tmem_ld16(base + gb, re);

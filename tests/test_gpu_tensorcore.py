@@ -82,8 +82,8 @@ def test_tensorcore_matches_fp32_path_and_empty_slice():
     op = oracle_plan(g)
     assert not (np.isin(op.j0, [2]) | np.isin(op.j1, [2])).any()
     X = gt.apply_stage(4, gt.apply_stage(3, dev(interleave(ds))))
-    Xh = host(X).reshape(gt.info.nbins, g.nq, g.ntheta, G)
-    assert np.all(Xh[:, :, 2, :] == 0) and np.any(Xh[:, :, 1, :] != 0)
+    Xh = host(X).reshape(g.ntheta, gt.info.nbins, g.nq, G)      # slice-major spectra
+    assert np.all(Xh[2] == 0) and np.any(Xh[1] != 0)
 
 
 def test_tensorcore_rejects_unsupported():
