@@ -19,6 +19,8 @@ What it computes (paper sections and equations):
 * ``nudft.c``   the direct sum of that slice step (FP64, OpenMP over bins).
 * ``fista``     soft shrinkage (eq. soft), ISTA (eq. ISTA) and its FISTA
                 momentum variant, power iteration for the step length.
+* ``decon``     the deconvolutive operator W L of eq. DecRT (time convolution
+                with a wavelet) and its transpose.
 * ``checks``    independent evaluations used only to pin the oracle: the
                 physical-domain Riemann sum along the azimuth-dependent
                 hyperbolae (eq. Inverse, Sec. 5.1) and the time-domain
@@ -33,4 +35,4 @@ the soft threshold's piecewise form, ISTA monotonicity, KKT optimality and
 spike recovery.  Every function in this package is covered by at least one.
 """
 from .plan import OraclePlan, make_plan            # noqa: F401
-from . import ops, fista, checks                    # noqa: F401
+from . import ops, fista, checks, decon             # noqa: F401

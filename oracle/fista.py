@@ -44,27 +44,39 @@ def momentum_schedule(iters: int):
     return np.array(out)
 
 
-def power_sigma2(plan, d, iters: int = 30, impl: str = "c") -> float:
+def _pair(plan, impl, op):
+    """(forward, adjoint) callables: L and L^T, or the given pair."""
+    if op is not None:
+        return op
+    return (lambda m: ops.forward(plan, m, impl)), (lambda d: ops.adjoint(plan, d, impl))
+
+
+def power_sigma2(plan, d, iters: int = 30, impl: str = "c", op=None) -> float:
     """Estimate of the largest eigenvalue of L^T L by power iteration from
-    L^T d / ||L^T d|| (Rayleigh quotient of the last iterate)."""
-    v = ops.adjoint(plan, d, impl)
+    L^T d / ||L^T d|| (Rayleigh quotient of the last iterate).  `op` may give
+    another (forward, adjoint) pair, e.g. the deconvolutive operator."""
+    fwd, adj = _pair(plan, impl, op)
+    v = adj(d)
     v = v / np.linalg.norm(v)
     lam = 0.0
     for _ in range(iters):
-        w = ops.adjoint(plan, ops.forward(plan, v, impl), impl)
+        w = adj(fwd(v))
         lam = float(np.vdot(v, w).real)
         v = w / np.linalg.norm(w)
     return lam
 
 
-def objective(plan, d, m, lam, impl: str = "c") -> float:
-    r = d - ops.forward(plan, m, impl)
+def objective(plan, d, m, lam, impl: str = "c", op=None) -> float:
+    fwd, _ = _pair(plan, impl, op)
+    r = d - fwd(m)
     return 0.5 * float(np.sum(r * r)) + lam * float(np.sum(np.abs(m)))
 
 
 def solve(plan, d, lam, iters, gamma, momentum: bool = True, m0=None,
-          impl: str = "c", history: bool = False):
-    """Run `iters` iterations of ISTA (momentum off) or FISTA (on)."""
+          impl: str = "c", history: bool = False, op=None):
+    """Run `iters` iterations of ISTA (momentum off) or FISTA (on); `op`
+    replaces (L, L^T) by another pair (the deconvolutive W L, L^T W^T)."""
+    fwd, adj = _pair(plan, impl, op)
     d = np.asarray(d, np.float64)
     shape = (plan.ntau, plan.nq, plan.ntheta)
     m = np.zeros(shape) if m0 is None else np.array(m0, np.float64)
@@ -72,7 +84,7 @@ def solve(plan, d, lam, iters, gamma, momentum: bool = True, m0=None,
     t = 1.0
     hist = []
     for _ in range(iters):
-        g = ops.adjoint(plan, d - ops.forward(plan, z, impl), impl)
+        g = adj(d - fwd(z))
         m_new = soft(z + gamma * g, gamma * lam)
         if momentum:
             tn = 0.5 * (1.0 + np.sqrt(1.0 + 4.0 * t * t))
@@ -82,7 +94,7 @@ def solve(plan, d, lam, iters, gamma, momentum: bool = True, m0=None,
             z = m_new
         m = m_new
         if history:
-            hist.append(objective(plan, d, m, lam, impl))
+            hist.append(objective(plan, d, m, lam, impl, op))
     return (m, hist) if history else m
 
 
