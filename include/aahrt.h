@@ -248,6 +248,30 @@ int aahrt_sparse_solve(aahrt_plan *plan, const float *d, float lambda,
                        int iters, float *m, const aahrt_solve_opts *opts,
                        aahrt_solve_info *info, void *stream);
 
+/* Automatic anisotropic velocity picking (Sec. 3.3, eq. vel_est): for a
+ * Radon model m (model_len floats, the plan's layout) writes, at every
+ * (tau, theta) of every cube or gather, the squared-slowness estimate
+ *   q_hat = sum_l q_l |m(tau, q_l, theta)| / sum_l |m(tau, q_l, theta)|
+ * (v^-2; the paper's ratio of q-moments with |m| as weights) and, when
+ * weight is non-NULL, the weight sum_l |m| (q_hat = 0 where it is 0).
+ * q_hat and weight hold model_len / nq floats: [g][tau][theta], or
+ * [tau][theta][g] for AAHRT_PRECISION_SPLIT_BF16 plans.  Device memory,
+ * 16-byte aligned; FP64 accumulation; stream-ordered. */
+int aahrt_pick_velocity(aahrt_plan *plan, const float *m, float *q_hat,
+                        float *weight, void *stream);
+
+/* Deconvolutive AAHRT (Sec. 4, eq. DecRT): after this call the plan's
+ * operator is W L, W the linear convolution of every trace with the wavelet
+ * in time (the band-limited wavelet replaces the Dirac pulse of the basis
+ * functions), truncated to the trace length:
+ *   (W x)[i] = sum_s w[s] x[i - s + center],  x = 0 outside [0, nt),
+ * and the adjoint L^T W^T.  aahrt_forward, aahrt_adjoint, aahrt_sparse_solve,
+ * aahrt_fista_vjp and aahrt_forward_noalloc all use it; aahrt_apply_stage
+ * does not.  w: host array of nw (1..4096) finite samples, center in
+ * [0, nw); nw = 0 restores the plain operator.  Synchronises the device
+ * (allocates the wavelet and a data-sized workspace on first use). */
+int aahrt_plan_set_wavelet(aahrt_plan *plan, const float *w, int nw, int center);
+
 /* Derivative of the unrolled sparse solve (configuration of Sec. 4 used as a
  * differentiable layer).  With m^n(d) the result of `iters` iterations of
  * aahrt_sparse_solve from m^0 = 0 at the given gamma and lambda (FISTA, or

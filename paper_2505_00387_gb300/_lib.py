@@ -84,6 +84,8 @@ _SIGS = {
     "aahrt_apply_stage": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "aahrt_fista_vjp": (c_int, [c_void_p, c_void_p, c_void_p, c_float, c_float, c_int, c_int,
                                 c_int, c_void_p, c_void_p, c_void_p]),
+    "aahrt_plan_set_wavelet": (c_int, [c_void_p, c_void_p, c_int, c_int]),
+    "aahrt_pick_velocity": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "aahrt_forward_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "aahrt_q_from_slowness": (c_int, [c_double, c_double, c_int, POINTER(c_double),
                                       POINTER(c_double)]),
@@ -203,6 +205,17 @@ def aahrt_plan_stage_times(h):
     n = (c_longlong * AAHRT_NSTAGES)()
     check(load().aahrt_plan_stage_times(h, t, n), "aahrt_plan_stage_times")
     return list(t), list(n)
+
+
+def aahrt_plan_set_wavelet(h, w_ptr, nw: int, center: int):
+    check(load().aahrt_plan_set_wavelet(h, c_void_p(w_ptr) if w_ptr else None, int(nw),
+                                        int(center)), "aahrt_plan_set_wavelet")
+
+
+def aahrt_pick_velocity(h, m_ptr: int, qhat_ptr: int, weight_ptr, stream: int = 0):
+    check(load().aahrt_pick_velocity(h, c_void_p(m_ptr), c_void_p(qhat_ptr),
+                                     c_void_p(weight_ptr) if weight_ptr else None,
+                                     c_void_p(stream)), "aahrt_pick_velocity")
 
 
 def aahrt_plan_status(h):

@@ -144,11 +144,23 @@ static cudaError_t reduce(Plan &p, const float *x, const float *y, long long n, 
 }
 
 // ------------------------------------------------------------ operators
+// With a wavelet set (deconvolutive operator W L), the synthesis writes L m
+// to the workspace and the time convolution produces d = W L m (or the
+// residual dobs - W L m); the adjoint correlates first (W^T d).
 int apply_forward(Plan &p, const float *m, float *d, cudaStream_t st, int epi,
                   const float *dobs, bool blocked) {
     cudaError_t e;
     if ((e = launch_r2c(p, true, m, p.X, st, blocked))) return cuda_fail(e, "stretch+FFT launch");
     if ((e = launch_slice(p, false, p.X, p.Y, st))) return cuda_fail(e, "slice launch");
+    if (p.nw > 0) {
+        if ((e = launch_c2r(p, false, p.Y, p.wtmp, EPI_STORE, nullptr, FistaArgs{}, st, blocked)))
+            return cuda_fail(e, "inverse FFT+unstretch launch");
+        prof_begin(p, 2, st);
+        e = launch_wavelet(p, epi == EPI_RESIDUAL ? 1 : 0, p.wtmp, d, dobs, st, blocked);
+        prof_end(p, st);
+        p.launches[2]++;
+        return e ? cuda_fail(e, "wavelet convolution launch") : AAHRT_OK;
+    }
     if ((e = launch_c2r(p, false, p.Y, d, epi, dobs, FistaArgs{}, st, blocked)))
         return cuda_fail(e, "inverse FFT+unstretch launch");
     return AAHRT_OK;
@@ -157,6 +169,14 @@ int apply_forward(Plan &p, const float *m, float *d, cudaStream_t st, int epi,
 int apply_adjoint(Plan &p, const float *d, float *m, cudaStream_t st, int epi, FistaArgs fa,
                   bool blocked) {
     cudaError_t e;
+    if (p.nw > 0) {
+        prof_begin(p, 3, st);
+        e = launch_wavelet(p, 2, d, p.wtmp, nullptr, st, blocked);
+        prof_end(p, st);
+        p.launches[3]++;
+        if (e) return cuda_fail(e, "wavelet correlation launch");
+        d = p.wtmp;
+    }
     if ((e = launch_r2c(p, false, d, p.Y, st, blocked)))
         return cuda_fail(e, "unstretch^T+FFT launch");
     if ((e = launch_slice(p, true, p.Y, p.X, st))) return cuda_fail(e, "slice adjoint launch");
@@ -529,10 +549,10 @@ static int solve(Plan &p, const float *d, float lambda, int iters, float *m,
         if (o.use_graph && !p.profiling) {
             char key[256];
             if (per_cube)
-                snprintf(key, sizeof key, "%d/cube/%d", iters, o.ista);
+                snprintf(key, sizeof key, "%d/cube/%d/w%d", iters, o.ista, p.wav_gen);
             else
-                snprintf(key, sizeof key, "%d/%.9g/%.9g/%d", iters, (double)fg, (double)fth,
-                         o.ista);
+                snprintf(key, sizeof key, "%d/%.9g/%.9g/%d/w%d", iters, (double)fg, (double)fth,
+                         o.ista, p.wav_gen);
             if (!p.gexec || p.gkey != key) {
                 if (p.gexec) { cudaGraphExecDestroy(p.gexec); p.gexec = nullptr; }
                 cudaStream_t cs;

@@ -153,6 +153,11 @@ struct Plan {
     int tc_gp = 0;                 // gathers padded to a multiple of 8
     int4 *tc_tiles = nullptr;      // forward row tiles {slice, first, end, 0}
     int tc_ntiles = 0;
+    // deconvolutive operator: wavelet convolved with every trace in time
+    float *wav = nullptr;          // nw samples (device)
+    int nw = 0, wcenter = 0;
+    int wav_gen = 0;               // bumped whenever the wavelet changes
+    float *wtmp = nullptr;         // data-sized workspace of the convolution
     // tiles
     bool autotuned = false;
     double tune_ms = 0;
@@ -196,6 +201,10 @@ cudaError_t launch_slice(Plan &p, bool adjoint, const float2 *in, float2 *out,
 cudaError_t launch_slice_tc(Plan &p, bool adjoint, const float2 *in, float2 *out,
                             cudaStream_t st, int *counter);
 cudaError_t configure_tc_kernels(Plan &p, int num_sms, int max_smem);
+// time convolution of the data columns with the plan's wavelet: mode 0 out = W in,
+// 1 out = aux - W in, 2 out = W^T in
+cudaError_t launch_wavelet(Plan &p, int mode, const float *in, float *out, const float *aux,
+                           cudaStream_t st, bool blocked);
 // device error flag of the tensor-core kernels (a timed-out wait), in Plan::counters
 constexpr int kTcErrSlot = 8;
 

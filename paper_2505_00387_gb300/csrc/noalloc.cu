@@ -78,8 +78,15 @@ extern "C" int aahrt_forward_noalloc(aahrt_plan *plan, const float *m, float *d,
         cudaError_t e;
         if ((e = launch_r2c(p, true, m, X, st))) { rc = cuda_fail(e, "stretch+FFT launch"); break; }
         if ((e = launch_slice(p, false, X, Y, st, counter))) { rc = cuda_fail(e, "slice launch"); break; }
-        if ((e = launch_c2r(p, false, Y, d, EPI_STORE, nullptr, FistaArgs{}, st))) {
+        // deconvolutive plans: synthesis into the plan's (preallocated)
+        // convolution workspace, then the time convolution into d
+        float *dsyn = p.nw > 0 ? p.wtmp : d;
+        if ((e = launch_c2r(p, false, Y, dsyn, EPI_STORE, nullptr, FistaArgs{}, st))) {
             rc = cuda_fail(e, "inverse FFT+unstretch launch");
+            break;
+        }
+        if (p.nw > 0 && (e = launch_wavelet(p, 0, dsyn, d, nullptr, st, false))) {
+            rc = cuda_fail(e, "wavelet convolution launch");
             break;
         }
     } while (0);

@@ -183,7 +183,7 @@ void free_plan(Plan *p) {
                     p->cg_model, p->cg_data, p->cg_model_blk, p->cg_data_blk, p->posS,
                     p->posU, p->rngST, p->rngUT, p->X, p->Y, p->z, p->r, p->v, p->scal,
                     p->stage_m, p->stage_d, p->zb, p->mb, p->rb, p->db, p->vjp_ws,
-                    p->cube_gt, p->cube_acc, p->dseg, p->tc_tiles};
+                    p->cube_gt, p->cube_acc, p->dseg, p->tc_tiles, p->wav, p->wtmp};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     cudaSetDevice(cur);

@@ -177,6 +177,26 @@ class AahrtPlan:
                             _stream_ptr(stream))
         return out
 
+    def pick_velocity(self, m: torch.Tensor, stream=None):
+        """(q_hat, weight): the q-moment pick of eq. vel_est at every
+        (tau, theta) (see aahrt_pick_velocity)."""
+        self._check(m, self.model_len, "m")
+        n = self.model_len // self.nq
+        q_hat = torch.empty(n, device=m.device, dtype=torch.float32)
+        weight = torch.empty(n, device=m.device, dtype=torch.float32)
+        L.aahrt_pick_velocity(self.handle, m.data_ptr(), q_hat.data_ptr(), weight.data_ptr(),
+                              _stream_ptr(stream))
+        return q_hat, weight
+
+    def set_wavelet(self, w, center: int):
+        """Make the operator the deconvolutive W L (eq. DecRT): every trace
+        convolved in time with w (sample `center` at lag 0); None clears."""
+        if w is None:
+            L.aahrt_plan_set_wavelet(self.handle, 0, 0, 0)
+            return
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        L.aahrt_plan_set_wavelet(self.handle, w.ctypes.data, int(w.size), int(center))
+
     def status(self):
         """Synchronise; raise AahrtError if a kernel reported a device-side
         timeout since the last check."""
