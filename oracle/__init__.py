@@ -22,6 +22,8 @@ What it computes (paper sections and equations):
 * ``decon``     the deconvolutive operator W L of eq. DecRT (time convolution
                 with a wavelet) and its transpose.
 * ``pick``      the q-moment velocity pick of eq. vel_est.
+* ``lineark``   the paper-literal slice step: linear interpolation in k of
+                the FFT'd q columns (A-coefficients of eq. thli).
 * ``checks``    independent evaluations used only to pin the oracle: the
                 physical-domain Riemann sum along the azimuth-dependent
                 hyperbolae (eq. Inverse, Sec. 5.1) and the time-domain
@@ -36,4 +38,4 @@ the soft threshold's piecewise form, ISTA monotonicity, KKT optimality and
 spike recovery.  Every function in this package is covered by at least one.
 """
 from .plan import OraclePlan, make_plan            # noqa: F401
-from . import ops, fista, checks, decon, pick       # noqa: F401
+from . import ops, fista, checks, decon, pick, lineark   # noqa: F401
