@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="gather", choices=["gather", "batch512"])
+    ap.add_argument("--workload", default="gather", choices=["gather", "batch512", "table1"])
     return ap.parse_args()
 
 
@@ -503,9 +503,75 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# The paper's Table 1: adjoint (velocity scan) of regular Nx x Ny offset
+# grids at dx = dy = 40 m, dt = 4 ms, 90 azimuths; (Nt, Nx, Ny, Np) and the
+# paper's "proposed" seconds (hardware not stated in the paper).
+TABLE1 = [(512, 128, 128, 128, 0.87), (512, 128, 128, 256, 1.14),
+          (512, 256, 256, 128, 3.80), (512, 256, 256, 256, 3.98),
+          (1024, 128, 128, 128, 1.97), (1024, 128, 128, 256, 2.78),
+          (1024, 256, 256, 128, 8.57), (1024, 256, 256, 256, 8.82)]
+
+
+def run_table1(args):
+    """Adjoint time at the Table 1 shapes for both slice steps (the accurate
+    spreading kernel and the paper's linear k-interpolation at sigma_q = 1)."""
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    from paper_2505_00387_gb300 import build as B
+    B.build()
+    from paper_2505_00387_gb300 import synthetic as syn
+    from paper_2505_00387_gb300.plan import AahrtPlan
+
+    rows = []
+    total = 0.0
+    for nt, nx, ny, npq, paper_s in TABLE1:
+        x = (np.arange(nx) - nx / 2 + 0.5) * 40.0
+        y = (np.arange(ny) - ny / 2 + 0.5) * 40.0
+        hx, hy = np.meshgrid(x, y, indexing="ij")
+        hx, hy = hx.ravel(), hy.ravel()
+        q0, dq = syn.q_axis(npq)
+        row = {"nt": nt, "nx": nx, "ny": ny, "np": npq, "ntheta": 90, "paper_s": paper_s}
+        for mode, kw in (("spread", {}), ("linear_k", dict(slice_interp="linear_k",
+                                                           sigma_q=1.0))):
+            gp = AahrtPlan(nt, 0.004, nt, npq, q0, dq, 90, hx, hy, **kw)
+            d = torch.randn(gp.data_len, device="cuda")
+            m = torch.empty(gp.model_len, device="cuda")
+            for _ in range(max(args.warmup, 3)):
+                gp.adjoint(d, m)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.steps):
+                gp.adjoint(d, m)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            row[mode + "_ms"] = round(ms, 3)
+            row["nfft"] = gp.info.nfft
+            if mode == "spread":
+                total += ms
+            del gp, d, m
+            torch.cuda.empty_cache()
+        rows.append(row)
+    line = {"metric": "AAHRT adjoint (velocity scan) time at the paper's Table 1 shapes",
+            "value": round(total, 3), "unit": "ms (sum over the 8 shapes, accurate slice step)",
+            "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 3),
+            "higher_is_better": False, "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (random data on regular offset grids)",
+            "config": {"workload": "Table 1: regular Nx x Ny grids, dx = dy = 40 m, "
+                                   "dt = 4 ms, 90 azimuths, q over 1/3500..1/1500 s/m"},
+            "shapes": rows}
+    print(json.dumps(line), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "table1":
+        run_table1(a)
     else:
         run_ours(a)

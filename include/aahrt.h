@@ -82,6 +82,17 @@ extern "C" {
  *   every FP32 operand split into two bf16 parts (three products, FP32
  *   accumulation; about 1e-5 relative).  Its model and data buffers hold the
  *   gathers fastest: m[tau][q][theta][g], d[t][trace][g]. */
+/* Slice-step interpolation of the FP32 path.
+ * AAHRT_SLICE_SPREAD: exponential-of-semicircle spreading kernel with
+ *   deapodisation (the accurate non-uniform DFT along q, default).
+ * AAHRT_SLICE_LINEAR_K: the paper's own step 3 (A-coefficients of eq. thli):
+ *   FFT of the centred, zero-padded q columns and linear interpolation
+ *   between the two neighbouring k samples, no deapodisation (second-order
+ *   in the k spacing: about 30 % error at sigma_q = 1, 8 % at 2 on smooth
+ *   events; see the design notes).  The adjoint is its exact transpose. */
+#define AAHRT_SLICE_SPREAD 0
+#define AAHRT_SLICE_LINEAR_K 1
+
 #define AAHRT_PRECISION_FP32 0
 #define AAHRT_PRECISION_SPLIT_BF16 1
 
@@ -121,6 +132,10 @@ typedef struct {
                            at plan creation (see aahrt_plan_create); fields
                            set explicitly above are kept */
     int precision;      /* AAHRT_PRECISION_FP32 (0) or AAHRT_PRECISION_SPLIT_BF16 */
+    int slice_interp;   /* AAHRT_SLICE_SPREAD (0) or AAHRT_SLICE_LINEAR_K */
+    double sigma_q;     /* q grid oversampling: the grid has max(16,
+                           next_pow2(ceil(sigma_q nq))) points; 0 = 2; the
+                           spreading kernel needs >= 1.25 nq points */
 } aahrt_opts;
 
 /* What a plan chose (filled by aahrt_plan_query). */

@@ -20,6 +20,8 @@ AAHRT_ERR_TIMEOUT = -5
 AAHRT_ERR_NONFINITE = -6
 AAHRT_INTERP_KEYS = 0
 AAHRT_INTERP_LINEAR = 1
+AAHRT_SLICE_SPREAD = 0
+AAHRT_SLICE_LINEAR_K = 1
 AAHRT_PRECISION_FP32 = 0
 AAHRT_PRECISION_SPLIT_BF16 = 1
 AAHRT_NSTAGES = 7
@@ -36,7 +38,8 @@ class aahrt_geom(ctypes.Structure):
 class aahrt_opts(ctypes.Structure):
     _fields_ = [("interp_kind", c_int), ("spread_width", c_int), ("theta_group", c_int),
                 ("ngather", c_int), ("sigma_t", c_double), ("fmax", c_double),
-                ("time_pairs", c_int), ("autotune", c_int), ("precision", c_int)]
+                ("time_pairs", c_int), ("autotune", c_int), ("precision", c_int),
+                ("slice_interp", c_int), ("sigma_q", c_double)]
 
 
 class aahrt_plan_info(ctypes.Structure):

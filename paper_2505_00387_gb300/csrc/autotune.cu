@@ -143,7 +143,8 @@ int autotune_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
     // reference plan (widest kernel) fixes the buffer sizes of the trial batch
     Plan *ref = nullptr;
     aahrt_opts o = base;
-    o.spread_width = kMaxW;
+    const bool lineark = base.slice_interp == AAHRT_SLICE_LINEAR_K;
+    if (!lineark) o.spread_width = kMaxW;
     if ((rc = make(o, &ref))) return rc;
     const long long nm = ref->model_len, nd = ref->data_len;
     DevBuf bm, bd, bd2, bg, bacc;
@@ -163,7 +164,7 @@ int autotune_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
 
     // spreading width: smallest with measured relative error <= 2e-6
     int W = base.spread_width;
-    if (W == 0) {
+    if (W == 0 && !lineark) {
         W = kMaxW;
         for (int w = kMinW + 1; w < kMaxW; ++w) {
             Plan *pw = nullptr;

@@ -150,6 +150,7 @@ struct Plan {
     long long *dseg = nullptr;     // data offsets of the cubes (ncube + 1 entries)
     // tensor-core direct contraction (precision 1): gathers stored fastest
     int precision = 0;
+    int slice_interp = 0;          // AAHRT_SLICE_SPREAD or AAHRT_SLICE_LINEAR_K
     int tc_gp = 0;                 // gathers padded to a multiple of 8
     int4 *tc_tiles = nullptr;      // forward row tiles {slice, first, end, 0}
     int tc_ntiles = 0;

@@ -236,8 +236,18 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
     if (opts.interp_kind != AAHRT_INTERP_KEYS && opts.interp_kind != AAHRT_INTERP_LINEAR)
         return set_error(AAHRT_ERR_INVALID_ARG, "interp_kind must be 0 or 1");
     int W = opts.spread_width;
-    if (W != 0 && (W < kMinW || W > kMaxW))
+    const bool lineark = opts.slice_interp == AAHRT_SLICE_LINEAR_K;
+    if (opts.slice_interp != AAHRT_SLICE_SPREAD && !lineark)
+        return set_error(AAHRT_ERR_INVALID_ARG, "slice_interp must be 0 or 1");
+    if (lineark) {
+        if (W != 0 && W != 2)
+            return set_error(AAHRT_ERR_INVALID_ARG, "linear k-interpolation has 2 taps");
+        W = 2;
+    } else if (W != 0 && (W < kMinW || W > kMaxW)) {
         return set_error(AAHRT_ERR_INVALID_ARG, "spread_width must be in [%d, %d]", kMinW, kMaxW);
+    }
+    if (!(opts.sigma_q == 0.0 || (opts.sigma_q >= 1.0 && opts.sigma_q <= 16.0)))
+        return set_error(AAHRT_ERR_INVALID_ARG, "sigma_q must be 0 (default 2) or in [1, 16]");
     if (opts.sigma_t < 0.0 || (opts.sigma_t > 0.0 && opts.sigma_t < 1.0))
         return set_error(AAHRT_ERR_INVALID_ARG, "sigma_t must be 0 (default) or >= 1");
     if (opts.fmax < 0.0 || opts.theta_group < 0 || opts.ngather < 0)
@@ -258,6 +268,9 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
         if (G_tc > 64 || g0.nq > 256)
             return set_error(AAHRT_ERR_UNSUPPORTED,
                              "the tensor-core contraction supports ngather <= 64, nq <= 256");
+        if (lineark)
+            return set_error(AAHRT_ERR_UNSUPPORTED,
+                             "the tensor-core contraction evaluates the exact DFT along q");
         ncube = 1;
     }
 
@@ -311,10 +324,18 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
     p->lp = ilog2(p->pairs);
 
     // ----------------------------------------------------- q spreading
-    p->nos = (int)std::max(16LL, next_pow2(2LL * p->nq));
+    const double sq = opts.sigma_q > 0.0 ? opts.sigma_q : 2.0;
+    p->nos = (int)std::max(16LL, next_pow2((long long)std::ceil(sq * p->nq - 1e-9)));
     p->Lq = ilog2(p->nos);
     p->cq = p->nq / 2;
+    p->slice_interp = opts.slice_interp;
     const double sigma_q = (double)p->nos / p->nq;
+    if (!lineark && sigma_q < 1.25) {
+        rc_fail = set_error(AAHRT_ERR_UNSUPPORTED, "the spreading kernel needs a q grid of at "
+                            "least 1.25 nq points (sigma_q)");
+        free_plan(p);
+        return rc_fail;
+    }
     if (W == 0) {
         // smallest width whose spreading error exp(-pi W sqrt(1 - 1/sigma))
         // is below 1e-6 (about 2e-6 measured for sigma = 2..2.6)
@@ -325,7 +346,8 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
     p->beta = 0.97 * M_PI * W * (1.0 - 1.0 / (2.0 * sigma_q));
     std::vector<float> dec(p->nq);
     for (int l = 0; l < p->nq; ++l)
-        dec[l] = (float)(1.0 / es_fourier((double)(l - p->cq) / p->nos, p->beta, W));
+        dec[l] = lineark ? 1.0f
+                         : (float)(1.0 / es_fourier((double)(l - p->cq) / p->nos, p->beta, W));
 
     // --------------------------------------------------- azimuth groups
     const size_t per_slice = (size_t)std::max(ld_interleaved(p->nos), ld_split(p->nos)) *
@@ -488,7 +510,16 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
         free_plan(p);
         return rc_fail;
     }
-    fit_es_poly(W, p->beta, &p->poly);
+    if (lineark) {
+        // two taps at grid points u0, u0 + 1 with g = a - 1/2: 1/2 - g and 1/2 + g
+        std::memset(&p->poly, 0, sizeof p->poly);
+        p->poly.c[0][0] = 0.5f;
+        p->poly.c[1][0] = -1.0f;
+        p->poly.c[0][1] = 0.5f;
+        p->poly.c[1][1] = 1.0f;
+    } else {
+        fit_es_poly(W, p->beta, &p->poly);
+    }
     {   // bound on the summed kernel weights of one trace, with margin
         double mx = 0.0;
         for (int s = 0; s <= 2000; ++s) {

@@ -387,7 +387,7 @@ static SliceArgs make_args(const Plan &p, int counter_slot) {
     return a;
 }
 
-#define AAHRT_W_CASES(X) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12)
+#define AAHRT_W_CASES(X) X(2) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12)
 
 cudaError_t launch_slice(Plan &p, bool adjoint, const float2 *in, float2 *out,
                          cudaStream_t st, int *counter) {

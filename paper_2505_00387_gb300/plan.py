@@ -33,12 +33,16 @@ def _geom(nt, dt, ntau, nq, q0, dq, ntheta, hx, hy, keep):
 PRECISIONS = {"fp32": L.AAHRT_PRECISION_FP32, "split_bf16": L.AAHRT_PRECISION_SPLIT_BF16}
 
 
+SLICE_INTERPS = {"spread": L.AAHRT_SLICE_SPREAD, "linear_k": L.AAHRT_SLICE_LINEAR_K}
+
+
 def _opts(interp="keys", spread_width=0, theta_group=0, ngather=1, sigma_t=0.0, fmax=0.0,
-          time_pairs=0, autotune=False, precision="fp32"):
+          time_pairs=0, autotune=False, precision="fp32", slice_interp="spread",
+          sigma_q=0.0):
     kind = {"keys": L.AAHRT_INTERP_KEYS, "linear": L.AAHRT_INTERP_LINEAR}[interp]
     return L.aahrt_opts(kind, int(spread_width), int(theta_group), int(ngather),
                         float(sigma_t), float(fmax), int(time_pairs), int(bool(autotune)),
-                        PRECISIONS[precision])
+                        PRECISIONS[precision], SLICE_INTERPS[slice_interp], float(sigma_q))
 
 
 class AahrtPlan:
@@ -46,8 +50,8 @@ class AahrtPlan:
 
     def __init__(self, nt, dt, ntau, nq, q0, dq, ntheta, hx, hy, *, interp="keys",
                  spread_width=0, theta_group=0, ngather=1, sigma_t=0.0, fmax=0.0,
-                 time_pairs=0, autotune=False, precision="fp32", _handle=None,
-                 _shapes=None):
+                 time_pairs=0, autotune=False, precision="fp32", slice_interp="spread",
+                 sigma_q=0.0, _handle=None, _shapes=None):
         if _handle is not None:
             self.handle = _handle
         else:
@@ -55,7 +59,7 @@ class AahrtPlan:
             g = _geom(nt, dt, ntau, nq, q0, dq, ntheta, hx, hy, keep)
             self.handle = L.aahrt_plan_create(
                 g, _opts(interp, spread_width, theta_group, ngather, sigma_t, fmax,
-                         time_pairs, autotune, precision))
+                         time_pairs, autotune, precision, slice_interp, sigma_q))
         self.info = L.aahrt_plan_query(self.handle)
         self.nt, self.ntau, self.nq, self.ntheta = nt, ntau, nq, ntheta
         self.device = torch.device("cuda", torch.cuda.current_device())
@@ -66,13 +70,14 @@ class AahrtPlan:
 
     @classmethod
     def batched(cls, gathers: Sequence, interp="keys", spread_width=0, theta_group=0,
-                sigma_t=0.0, fmax=0.0, time_pairs=0, autotune=False):
+                sigma_t=0.0, fmax=0.0, time_pairs=0, autotune=False, slice_interp="spread",
+                sigma_q=0.0):
         keep = []
         geoms = [_geom(g.nt, g.dt, g.ntau, g.nq, g.q0, g.dq, g.ntheta, g.hx, g.hy, keep)
                  for g in gathers]
         h = L.aahrt_plan_create_batched(
             geoms, _opts(interp, spread_width, theta_group, 1, sigma_t, fmax, time_pairs,
-                         autotune))
+                         autotune, "fp32", slice_interp, sigma_q))
         g0 = gathers[0]
         return cls(g0.nt, g0.dt, g0.ntau, g0.nq, g0.q0, g0.dq, g0.ntheta, None, None,
                    _handle=h)
