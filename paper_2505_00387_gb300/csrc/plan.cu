@@ -355,7 +355,7 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
     if (opts.theta_group > 0) {
         p->tgroup = std::min(opts.theta_group, p->ntheta);
     } else {
-        const size_t budget = 80 * 1024;
+        const size_t budget = 72 * 1024;      // three blocks per SM
         if (p->ntheta * per_slice <= budget) {
             p->tgroup = p->ntheta;
         } else {

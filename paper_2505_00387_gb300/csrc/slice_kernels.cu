@@ -47,7 +47,7 @@ __device__ __forceinline__ int fast_div(int a, int d, float inv_d) {
 }
 
 template <int W>
-__global__ void __launch_bounds__(kThreadsSlice, 2)
+__global__ void __launch_bounds__(kThreadsSlice, 3)
 slice_fwd_kernel(const SliceArgs a, const float2 *__restrict__ X, float2 *__restrict__ Y) {
     extern __shared__ float4 smem_f4[];
     float2 *G = reinterpret_cast<float2 *>(smem_f4);
@@ -247,7 +247,7 @@ __device__ __forceinline__ void adj_last_step(const SliceArgs &a, const SliceGro
 }
 
 template <int W>
-__global__ void __launch_bounds__(kThreadsSlice, 2)
+__global__ void __launch_bounds__(kThreadsSlice, 3)
 slice_adj_kernel(const SliceArgs a, const float2 *__restrict__ Y, float2 *__restrict__ X) {
     extern __shared__ float4 smem_f4[];
     float *smf = reinterpret_cast<float *>(smem_f4);
