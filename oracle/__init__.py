@@ -24,6 +24,8 @@ What it computes (paper sections and equations):
 * ``pick``      the q-moment velocity pick of eq. vel_est.
 * ``lineark``   the paper-literal slice step: linear interpolation in k of
                 the FFT'd q columns (A-coefficients of eq. thli).
+* ``bpull``     the paper's velocity scan (Algorithm 2): data on a regular
+                offset grid pulled at the rings k = f' r^2 (B-coefficients).
 * ``checks``    independent evaluations used only to pin the oracle: the
                 physical-domain Riemann sum along the azimuth-dependent
                 hyperbolae (eq. Inverse, Sec. 5.1) and the time-domain
@@ -38,4 +40,4 @@ the soft threshold's piecewise form, ISTA monotonicity, KKT optimality and
 spike recovery.  Every function in this package is covered by at least one.
 """
 from .plan import OraclePlan, make_plan            # noqa: F401
-from . import ops, fista, checks, decon, pick, lineark   # noqa: F401
+from . import ops, fista, checks, decon, pick, lineark, bpull   # noqa: F401
