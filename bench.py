@@ -513,8 +513,10 @@ TABLE1 = [(512, 128, 128, 128, 0.87), (512, 128, 128, 256, 1.14),
 
 
 def run_table1(args):
-    """Adjoint time at the Table 1 shapes for both slice steps (the accurate
-    spreading kernel and the paper's linear k-interpolation at sigma_q = 1)."""
+    """Velocity-scan time at the Table 1 shapes: the exact adjoint with both
+    slice steps (the accurate spreading kernel and the paper's linear
+    k-interpolation at sigma_q = 1) and the paper's own pull scan on the
+    regular grid (Algorithm 2, B-coefficients)."""
     import numpy as np
     import torch
 
@@ -553,6 +555,17 @@ def run_table1(args):
             row["nfft"] = gp.info.nfft
             if mode == "spread":
                 total += ms
+                # the paper's own pull scan on the same grid (Algorithm 2)
+                grid = (nx, ny, float(x[0]), 40.0, float(y[0]), 40.0)
+                for _ in range(max(args.warmup, 3)):
+                    gp.velocity_scan_grid(d, grid, m)
+                torch.cuda.synchronize()
+                e0.record()
+                for _ in range(args.steps):
+                    gp.velocity_scan_grid(d, grid, m)
+                e1.record()
+                torch.cuda.synchronize()
+                row["pull_scan_ms"] = round(e0.elapsed_time(e1) / args.steps, 3)
             del gp, d, m
             torch.cuda.empty_cache()
         rows.append(row)

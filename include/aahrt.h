@@ -263,6 +263,30 @@ int aahrt_sparse_solve(aahrt_plan *plan, const float *d, float lambda,
                        int iters, float *m, const aahrt_solve_opts *opts,
                        aahrt_solve_info *info, void *stream);
 
+/* A regular offset grid: trace ix * ny + iy sits at (x0 + ix dx, y0 + iy dy). */
+typedef struct {
+    int nx, ny;
+    double x0, dx, y0, dy;
+} aahrt_grid;
+
+/* The paper's own velocity scan (Algorithm 2 with the B-coefficients of
+ * Sec. 3.4), for data recorded on a regular offset grid: the data time axis
+ * is stretched by interpolation and FFT'd; at every bin f' and azimuth slice
+ * theta_j the spectrum is read by bilinear interpolation at
+ * (x, y) = +-sqrt(k/f') (cos theta_j, sin theta_j) for every q-grid
+ * wavenumber k (all alias rings k + n/dq that stay inside the grid; both
+ * antipodal points, no Jacobian factor, bin 0 set to zero), inverse-DFT'd
+ * along k onto the q axis (centred on q_c = q0 + (nq/2) dq, with the phase
+ * exp(+2 pi i k q_c)), synthesised along f' (1/Nfft) and unstretched.  It is
+ * the paper's approximation of the velocity stack, not L^T (compare
+ * aahrt_adjoint).  The plan: single gather, AAHRT_PRECISION_FP32, ntau == nt,
+ * nq >= 2, ntr == nx * ny (its own offsets set only the stretched-time
+ * sampling); the q grid has nq_os points (opts.sigma_q).  d: data_len floats
+ * in grid trace order; m: model_len floats.  Device memory, stream-ordered;
+ * uses the plan's spectra workspace. */
+int aahrt_velocity_scan_grid(aahrt_plan *plan, const aahrt_grid *grid,
+                             const float *d, float *m, void *stream);
+
 /* Automatic anisotropic velocity picking (Sec. 3.3, eq. vel_est): for a
  * Radon model m (model_len floats, the plan's layout) writes, at every
  * (tau, theta) of every cube or gather, the squared-slowness estimate

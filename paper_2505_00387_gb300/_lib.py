@@ -52,6 +52,11 @@ class aahrt_plan_info(ctypes.Structure):
                 ("tune_ms", c_double), ("precision", c_int)]
 
 
+class aahrt_grid(ctypes.Structure):
+    _fields_ = [("nx", c_int), ("ny", c_int), ("x0", c_double), ("dx", c_double),
+                ("y0", c_double), ("dy", c_double)]
+
+
 class aahrt_solve_opts(ctypes.Structure):
     _fields_ = [("ista", c_int), ("warm_start", c_int), ("power_iters", c_int),
                 ("use_graph", c_int), ("gamma", c_double), ("lambda_rel", c_double),
@@ -89,6 +94,8 @@ _SIGS = {
                                 c_int, c_void_p, c_void_p, c_void_p]),
     "aahrt_plan_set_wavelet": (c_int, [c_void_p, c_void_p, c_int, c_int]),
     "aahrt_pick_velocity": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "aahrt_velocity_scan_grid": (c_int, [c_void_p, POINTER(aahrt_grid), c_void_p, c_void_p,
+                                         c_void_p]),
     "aahrt_forward_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "aahrt_q_from_slowness": (c_int, [c_double, c_double, c_int, POINTER(c_double),
                                       POINTER(c_double)]),
@@ -219,6 +226,12 @@ def aahrt_pick_velocity(h, m_ptr: int, qhat_ptr: int, weight_ptr, stream: int = 
     check(load().aahrt_pick_velocity(h, c_void_p(m_ptr), c_void_p(qhat_ptr),
                                      c_void_p(weight_ptr) if weight_ptr else None,
                                      c_void_p(stream)), "aahrt_pick_velocity")
+
+
+def aahrt_velocity_scan_grid(h, grid: aahrt_grid, d_ptr: int, m_ptr: int, stream: int = 0):
+    check(load().aahrt_velocity_scan_grid(h, ctypes.byref(grid), c_void_p(d_ptr),
+                                          c_void_p(m_ptr), c_void_p(stream)),
+          "aahrt_velocity_scan_grid")
 
 
 def aahrt_plan_status(h):

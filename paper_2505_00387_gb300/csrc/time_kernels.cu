@@ -380,3 +380,31 @@ cudaError_t set_time_kernel_attrs(int lp, int interp, int max_smem) {
 }
 
 }  // namespace aahrt
+
+namespace aahrt {
+
+// The model's stretch S applied to data columns, then the FFT (the first two
+// steps of the paper's velocity scan; needs ntau == nt).
+cudaError_t launch_stretch_data(Plan &p, const float *d, float2 *Y, cudaStream_t st) {
+    prof_begin(p, 3, st);
+    AAHRT_LP_SWITCH(p.lp, AAHRT_INTERP_SWITCH(p.interp, (r2c_launch<LPc, IPc>(
+        true, p.ncg_data, p.smem_r2c_model, st, d, Y, p.cg_data, p.S, p.nt, p.tw_t, p.L,
+        p.nbins))));
+    prof_end(p, st);
+    p.launches[3]++;
+    return cudaGetLastError();
+}
+
+// Hermitian synthesis and the stretch undone (U) on model columns (its last
+// steps; ntau == nt).
+cudaError_t launch_unstretch_model(Plan &p, const float2 *X, float *m, cudaStream_t st) {
+    prof_begin(p, 5, st);
+    AAHRT_LP_SWITCH(p.lp, AAHRT_INTERP_SWITCH(p.interp, (c2r_launch<LPc, IPc, EPI_STORE>(
+        false, p.ncg_model, p.smem_c2r_data, st, X, m, nullptr, FistaArgs{}, p.cg_model, p.U,
+        p.ns, p.tw_t, p.L, p.nbins))));
+    prof_end(p, st);
+    p.launches[5]++;
+    return cudaGetLastError();
+}
+
+}  // namespace aahrt

@@ -182,6 +182,20 @@ class AahrtPlan:
                             _stream_ptr(stream))
         return out
 
+    def velocity_scan_grid(self, d: torch.Tensor, grid, m: Optional[torch.Tensor] = None,
+                           stream=None):
+        """The paper's pull velocity scan (Algorithm 2) of data on a regular
+        grid (nx, ny, x0, dx, y0, dy); see aahrt_velocity_scan_grid."""
+        self._check(d, self.data_len, "d")
+        if m is None:
+            m = torch.empty(self.model_len, device=d.device, dtype=torch.float32)
+        self._check(m, self.model_len, "m")
+        nx, ny, x0, dx, y0, dy = grid
+        g = L.aahrt_grid(int(nx), int(ny), float(x0), float(dx), float(y0), float(dy))
+        L.aahrt_velocity_scan_grid(self.handle, g, d.data_ptr(), m.data_ptr(),
+                                   _stream_ptr(stream))
+        return m
+
     def pick_velocity(self, m: torch.Tensor, stream=None):
         """(q_hat, weight): the q-moment pick of eq. vel_est at every
         (tau, theta) (see aahrt_pick_velocity)."""
