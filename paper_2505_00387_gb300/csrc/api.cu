@@ -329,6 +329,31 @@ static int read_scalars(Plan &p, double *h, cudaStream_t st) {
 static int run_iterations(Plan &p, int iters, float gamma, float thresh,
                           const std::vector<double> &betas, const float2 *cube_gt,
                           cudaStream_t st) {
+    cudaError_t e;
+    if (p.nw == 0 && p.smem_fused_model > 0 && p.smem_fused_data > 0 && iters > 0) {
+        // Fused half-iterations: the stretch+FFT of z runs once up front, then
+        // per iteration slice -> (synthesis + residual + U^T FFT) -> slice^T
+        // -> (synthesis + update + stretch+FFT of the new z).  The same
+        // arithmetic as the unfused sequence, without the residual and z
+        // round trips; the last update skips the unused next stretch.
+        if ((e = launch_r2c(p, true, p.zb, p.X, st, true)))
+            return cuda_fail(e, "stretch+FFT launch");
+        for (int it = 0; it < iters; ++it) {
+            if ((e = launch_slice(p, false, p.X, p.Y, st))) return cuda_fail(e, "slice launch");
+            if ((e = launch_c2r_r2c(p, false, p.Y, p.db, FistaArgs{}, st)))
+                return cuda_fail(e, "fused data-side launch");
+            if ((e = launch_slice(p, true, p.Y, p.X, st)))
+                return cuda_fail(e, "slice adjoint launch");
+            FistaArgs fa{p.mb, p.zb, gamma, thresh, (float)betas[it], cube_gt};
+            if (it + 1 < iters) {
+                if ((e = launch_c2r_r2c(p, true, p.X, nullptr, fa, st)))
+                    return cuda_fail(e, "fused model-side launch");
+            } else if ((e = launch_c2r(p, true, p.X, nullptr, EPI_FISTA, nullptr, fa, st, true))) {
+                return cuda_fail(e, "inverse FFT+stretch^T launch");
+            }
+        }
+        return AAHRT_OK;
+    }
     for (int it = 0; it < iters; ++it) {
         int rc = apply_forward(p, p.zb, p.rb, st, EPI_RESIDUAL, p.db, true);
         if (rc) return rc;
@@ -570,7 +595,8 @@ static int solve(Plan &p, const float *d, float lambda, int iters, float *m,
                 cudaStreamDestroy(cs);
                 long long per = 0;
                 for (int s = 0; s < AAHRT_NSTAGES; ++s) {
-                    per += p.launches[s] - before[s];
+                    p.gstage[s] = p.launches[s] - before[s];
+                    per += p.gstage[s];
                 }
                 std::memcpy(p.launches, before, sizeof before);
                 if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
@@ -582,8 +608,8 @@ static int solve(Plan &p, const float *d, float lambda, int iters, float *m,
                 p.glaunches = per;
             }
             if ((e = cudaGraphLaunch(p.gexec, st))) return cuda_fail(e, "graph launch");
-            // each iteration launches one kernel per operator stage
-            for (int s = 0; s < 6; ++s) p.launches[s] += iters;
+            // the kernels the captured sequence launches, per stage
+            for (int s = 0; s < AAHRT_NSTAGES; ++s) p.launches[s] += p.gstage[s];
         } else {
             if ((rc = run_iterations(p, iters, fg, fth, betas, cgt, st))) return rc;
         }

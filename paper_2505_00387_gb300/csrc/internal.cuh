@@ -135,6 +135,8 @@ struct Plan {
     int slice_grid_fwd = 0, slice_grid_adj = 0;
     size_t smem_r2c_model = 0, smem_r2c_data = 0, smem_c2r_model = 0, smem_c2r_data = 0;
     size_t smem_sfwd = 0, smem_sadj = 0;
+    size_t smem_fused_model = 0;   // fused model half-iteration (0: not available)
+    size_t smem_fused_data = 0;    // fused data half-iteration (0: not available)
     // workspace
     float2 *X = nullptr, *Y = nullptr;
     long long x_len = 0, y_len = 0;
@@ -166,6 +168,7 @@ struct Plan {
     cudaGraphExec_t gexec = nullptr;
     std::string gkey;
     long long glaunches = 0;
+    long long gstage[AAHRT_NSTAGES] = {0};   // its launches per stage
     // accounting
     long long launches[AAHRT_NSTAGES] = {0};
     bool profiling = false;
@@ -199,6 +202,9 @@ cudaError_t launch_c2r(Plan &p, bool model_side, const float2 *in, float *out,
                        bool blocked = false);
 cudaError_t launch_slice(Plan &p, bool adjoint, const float2 *in, float2 *out,
                          cudaStream_t st, int *counter = nullptr);
+// fused synthesis + analysis of one FISTA half-iteration (column-blocked state)
+cudaError_t launch_c2r_r2c(Plan &p, bool model_side, float2 *spec, const float *aux,
+                           FistaArgs fa, cudaStream_t st);
 cudaError_t launch_slice_tc(Plan &p, bool adjoint, const float2 *in, float2 *out,
                             cudaStream_t st, int *counter);
 cudaError_t configure_tc_kernels(Plan &p, int num_sms, int max_smem);

@@ -590,6 +590,10 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
                        (size_t)p->nt * sizeof(float);
     p->smem_c2r_data = fftb;
     p->smem_c2r_model = fftb + (size_t)p->ns * sizeof(float);
+    // fused FISTA half-iterations: the synthesis' source fractions (S^T has
+    // ns of them) beside the analysis' staged rows
+    p->smem_fused_model = p->smem_r2c_model + (size_t)p->ns * sizeof(float);
+    p->smem_fused_data = p->smem_r2c_data;
     const size_t smem_r2c = std::max(p->smem_r2c_model, p->smem_r2c_data);
     const size_t smem_c2r = std::max(p->smem_c2r_model, p->smem_c2r_data);
     p->smem_sfwd = (size_t)(p->tgroup + (p->ngroup > 1 ? 1 : 0)) * ld_interleaved(p->nos) *
@@ -606,6 +610,8 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
         free_plan(p);
         return rc_fail;
     }
+    if ((int)p->smem_fused_model > max_smem) p->smem_fused_model = 0;
+    if ((int)p->smem_fused_data > max_smem) p->smem_fused_data = 0;
     // The dynamic shared memory limit is a property of each kernel function,
     // shared by every plan of the process: raise it to the device maximum once
     // so no plan lowers it under another.

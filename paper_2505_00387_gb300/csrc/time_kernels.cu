@@ -85,32 +85,17 @@ struct Acc {
     }
 };
 
+// The r2c pipeline after its input rows are staged in shared memory
+// (stg [row][2P] floats, sfr the source fractions of a transposed
+// resampler; the caller synchronised): resample onto the frame, FFT, unpack.
 template <int LP, int INTERP, bool TRANS>
-__global__ void __launch_bounds__(kThreadsTime, 2)
-r2c_kernel(const float *__restrict__ in, float2 *__restrict__ out,
-           const ColGroup *__restrict__ groups, DevResampler rs, int nrow_in,
-           const float2 *__restrict__ tw, int L, int nbins) {
+__device__ __forceinline__ void r2c_core(float2 *sm, const float *stg, const float *sfr,
+                                         const ColGroup &cg, const DevResampler &rs,
+                                         int nrow_in, const float2 *__restrict__ tw, int L,
+                                         int nbins, float2 *__restrict__ out) {
     constexpr int P = 1 << LP;
-    extern __shared__ float4 smem_f4[];
-    float2 *sm = reinterpret_cast<float2 *>(smem_f4);
-    const ColGroup cg = groups[blockIdx.x];
     const int N = 1 << L;
     const int ld = ld_interleaved(N);
-    float *stg = reinterpret_cast<float *>(sm + P * ld);          // staged input [row][2P]
-    float *sfr = stg + nrow_in * 2 * P;                           // source fractions (TRANS)
-
-    // stage the block's input columns (independent, coalesced loads)
-    const float *src = in + cg.real_off;
-    for (int idx = threadIdx.x; idx < nrow_in * 2 * P; idx += blockDim.x) {
-        const int r = idx >> (LP + 1);
-        const int c = idx & (2 * P - 1);
-        stg[idx] = c < cg.ncol ? __ldg(src + (long long)r * cg.ld_real + c) : 0.f;
-    }
-    if (TRANS)
-        for (int idx = threadIdx.x; idx < rs.npos; idx += blockDim.x)
-            sfr[idx] = __ldg(&rs.pos[idx].fr);
-    __syncthreads();
-
     // z_p[n] = sum_r G[n][r] (x_{2p} + i x_{2p+1})[r], one row n per thread
     const float2 *stg2 = reinterpret_cast<const float2 *>(stg);
     for (int n = threadIdx.x; n < N; n += blockDim.x) {
@@ -161,20 +146,48 @@ r2c_kernel(const float *__restrict__ in, float2 *__restrict__ out,
     }
 }
 
-template <int LP, int INTERP, bool TRANS, int EPI>
+template <int LP, int INTERP, bool TRANS>
 __global__ void __launch_bounds__(kThreadsTime, 2)
-c2r_kernel(const float2 *__restrict__ in, float *__restrict__ out,
-           const float *__restrict__ aux, FistaArgs fa,
-           const ColGroup *__restrict__ groups, DevResampler rs, int n_in,
+r2c_kernel(const float *__restrict__ in, float2 *__restrict__ out,
+           const ColGroup *__restrict__ groups, DevResampler rs, int nrow_in,
            const float2 *__restrict__ tw, int L, int nbins) {
     constexpr int P = 1 << LP;
     extern __shared__ float4 smem_f4[];
     float2 *sm = reinterpret_cast<float2 *>(smem_f4);
     const ColGroup cg = groups[blockIdx.x];
+    const int ld = ld_interleaved(1 << L);
+    float *stg = reinterpret_cast<float *>(sm + P * ld);          // staged input [row][2P]
+    float *sfr = stg + nrow_in * 2 * P;                           // source fractions (TRANS)
+
+    // stage the block's input columns (independent, coalesced loads)
+    const float *src = in + cg.real_off;
+    for (int idx = threadIdx.x; idx < nrow_in * 2 * P; idx += blockDim.x) {
+        const int r = idx >> (LP + 1);
+        const int c = idx & (2 * P - 1);
+        stg[idx] = c < cg.ncol ? __ldg(src + (long long)r * cg.ld_real + c) : 0.f;
+    }
+    if (TRANS)
+        for (int idx = threadIdx.x; idx < rs.npos; idx += blockDim.x)
+            sfr[idx] = __ldg(&rs.pos[idx].fr);
+    __syncthreads();
+    r2c_core<LP, INTERP, TRANS>(sm, stg, sfr, cg, rs, nrow_in, tw, L, nbins, out);
+}
+
+// The c2r pipeline of one column group.  With STAGE, the epilogue's real
+// rows (the residual, or the new extrapolated point z of the FISTA update)
+// also go to stg [row][2P] in shared memory for an r2c of the same columns
+// (the residual is then not written to global memory).
+template <int LP, int INTERP, bool TRANS, int EPI, bool STAGE>
+__device__ __forceinline__ void c2r_core(float2 *sm, float *sfr, const float2 *__restrict__ in,
+                                         float *__restrict__ out,
+                                         const float *__restrict__ aux, const FistaArgs &fa,
+                                         const ColGroup &cg, const DevResampler &rs, int n_in,
+                                         const float2 *__restrict__ tw, int L, int nbins,
+                                         float *stg) {
+    constexpr int P = 1 << LP;
     const int N = 1 << L;
     const int half = N >> 1;
     const int ld = ld_interleaved(N);
-    float *sfr = reinterpret_cast<float *>(sm + P * ld);
     const float2 *src = in + cg.spec_off;
     const int npair = (cg.ncol + 1) >> 1;
 
@@ -188,8 +201,10 @@ c2r_kernel(const float2 *__restrict__ in, float *__restrict__ out,
         float2 zk = make_float2(0.f, 0.f), zn = zk;
         if (k < nbins && p < npair) {
             const long long o = (long long)k * cg.ld_spec + 2 * p;
-            float2 A = __ldg(src + o);
-            float2 B = (2 * p + 1 < cg.ncol) ? __ldg(src + o + 1) : make_float2(0.f, 0.f);
+            // the fused kernel rewrites the spectrum later: plain loads there
+            float2 A = STAGE ? src[o] : __ldg(src + o);
+            float2 B = (2 * p + 1 < cg.ncol) ? (STAGE ? src[o + 1] : __ldg(src + o + 1))
+                                             : make_float2(0.f, 0.f);
             if (k == 0) { A.y = 0.f; B.y = 0.f; }
             zk = make_float2(A.x - B.y, A.y + B.x);   // A + iB
             zn = make_float2(A.x + B.y, B.x - A.y);   // conj(A) + i conj(B)
@@ -247,9 +262,14 @@ c2r_kernel(const float2 *__restrict__ in, float *__restrict__ out,
             float dv[2 * P];
 #pragma unroll
             for (int c = 0; c < 2 * P; ++c) dv[c] = c < nc ? __ldg(aux + o + c) : 0.f;
+            if (STAGE) {
 #pragma unroll
-            for (int c = 0; c < 2 * P; ++c)
-                if (c < nc) out[o + c] = dv[c] - g2[c];
+                for (int c = 0; c < 2 * P; ++c) stg[i * 2 * P + c] = c < nc ? dv[c] - g2[c] : 0.f;
+            } else {
+#pragma unroll
+                for (int c = 0; c < 2 * P; ++c)
+                    if (c < nc) out[o + c] = dv[c] - g2[c];
+            }
         } else {
             // m+ = soft(z + gamma g, gamma lambda); z+ = m+ + beta (m+ - m)
             float gam = fa.gamma, th = fa.thresh;
@@ -268,13 +288,65 @@ c2r_kernel(const float2 *__restrict__ in, float *__restrict__ out,
             }
 #pragma unroll
             for (int c = 0; c < 2 * P; ++c) {
-                if (c >= nc) break;
+                if (c >= nc) {
+                    if (STAGE) stg[i * 2 * P + c] = 0.f;
+                    continue;
+                }
                 const float mn = soft_threshold(fmaf(gam, g2[c], zo[c]), th);
+                const float zn = fmaf(fa.beta, mn - mo[c], mn);
                 mp[c] = mn;
-                zp[c] = fmaf(fa.beta, mn - mo[c], mn);
+                zp[c] = zn;
+                if (STAGE) stg[i * 2 * P + c] = zn;
             }
         }
     }
+}
+
+template <int LP, int INTERP, bool TRANS, int EPI>
+__global__ void __launch_bounds__(kThreadsTime, 2)
+c2r_kernel(const float2 *__restrict__ in, float *__restrict__ out,
+           const float *__restrict__ aux, FistaArgs fa,
+           const ColGroup *__restrict__ groups, DevResampler rs, int n_in,
+           const float2 *__restrict__ tw, int L, int nbins) {
+    constexpr int P = 1 << LP;
+    extern __shared__ float4 smem_f4[];
+    float2 *sm = reinterpret_cast<float2 *>(smem_f4);
+    const ColGroup cg = groups[blockIdx.x];
+    float *sfr = reinterpret_cast<float *>(sm + P * ld_interleaved(1 << L));
+    c2r_core<LP, INTERP, TRANS, EPI, false>(sm, sfr, in, out, aux, fa, cg, rs, n_in, tw, L,
+                                            nbins, nullptr);
+}
+
+// One FISTA half-iteration's two time stages on the same column group, fused:
+// the synthesis c2r (with its epilogue: residual on the data side, FISTA
+// update on the model side) stages its real rows in shared memory and the
+// analysis r2c of the other direction transforms them in place of a round
+// trip through global memory.  Data side: U H then U^T F (residual r = d - L z
+// never stored); model side: S^T H with the update, then S F of the new z
+// (the next iteration's first stage).  The spectrum is read and rewritten in
+// place: a block touches only its own columns.
+template <int LP, int INTERP, bool SYN_TRANS, int EPI>
+__global__ void __launch_bounds__(kThreadsTime, 2)
+c2r_r2c_kernel(float2 *spec, const float *__restrict__ aux, FistaArgs fa,
+               const ColGroup *__restrict__ groups, DevResampler rs_syn, int n_in,
+               DevResampler rs_ana, int nrow_mid, const float2 *__restrict__ tw, int L,
+               int nbins) {
+    constexpr int P = 1 << LP;
+    constexpr bool ANA_TRANS = !SYN_TRANS;
+    extern __shared__ float4 smem_f4[];
+    float2 *sm = reinterpret_cast<float2 *>(smem_f4);
+    const ColGroup cg = groups[blockIdx.x];
+    float *stg = reinterpret_cast<float *>(sm + P * ld_interleaved(1 << L));   // [row][2P]
+    float *sfr = stg + nrow_mid * 2 * P;
+    c2r_core<LP, INTERP, SYN_TRANS, EPI, true>(sm, sfr, spec, nullptr, aux, fa, cg, rs_syn, n_in,
+                                               tw, L, nbins, stg);
+    __syncthreads();
+    if (ANA_TRANS) {
+        for (int idx = threadIdx.x; idx < rs_ana.npos; idx += blockDim.x)
+            sfr[idx] = __ldg(&rs_ana.pos[idx].fr);
+        __syncthreads();
+    }
+    r2c_core<LP, INTERP, ANA_TRANS>(sm, stg, sfr, cg, rs_ana, nrow_mid, tw, L, nbins, spec);
 }
 
 // ------------------------------------------------------------- dispatch
@@ -370,7 +442,33 @@ static cudaError_t attrs_for(int max_smem) {
     if ((e = raise_smem_limit(c2r_kernel<LPc, IPc, false, EPI_RESIDUAL>, max_smem))) return e;
     if ((e = raise_smem_limit(c2r_kernel<LPc, IPc, true, EPI_RESIDUAL>, max_smem))) return e;
     if ((e = raise_smem_limit(c2r_kernel<LPc, IPc, false, EPI_FISTA>, max_smem))) return e;
+    if ((e = raise_smem_limit(c2r_r2c_kernel<LPc, IPc, false, EPI_RESIDUAL>, max_smem))) return e;
+    if ((e = raise_smem_limit(c2r_r2c_kernel<LPc, IPc, true, EPI_FISTA>, max_smem))) return e;
     return raise_smem_limit(c2r_kernel<LPc, IPc, true, EPI_FISTA>, max_smem);
+}
+
+// Fused data-side (residual) or model-side (FISTA update + next stretch)
+// half-iteration on the column-blocked solver state, in place on the
+// spectrum (see c2r_r2c_kernel).
+cudaError_t launch_c2r_r2c(Plan &p, bool model_side, float2 *spec, const float *aux,
+                           FistaArgs fa, cudaStream_t st) {
+    const ColGroup *cg = model_side ? p.cg_model_blk : p.cg_data_blk;
+    const int n = model_side ? p.ncg_model : p.ncg_data;
+    const int stage = model_side ? 5 : 2;
+    prof_begin(p, stage, st);
+    if (model_side) {
+        AAHRT_LP_SWITCH(p.lp, AAHRT_INTERP_SWITCH(p.interp, (
+            c2r_r2c_kernel<LPc, IPc, true, EPI_FISTA><<<n, kThreadsTime, p.smem_fused_model, st>>>(
+                spec, nullptr, fa, cg, p.ST, p.ns, p.S, p.ntau, p.tw_t, p.L, p.nbins))));
+    } else {
+        AAHRT_LP_SWITCH(p.lp, AAHRT_INTERP_SWITCH(p.interp, (
+            c2r_r2c_kernel<LPc, IPc, false, EPI_RESIDUAL><<<n, kThreadsTime, p.smem_r2c_data,
+                                                           st>>>(
+                spec, aux, FistaArgs{}, cg, p.U, p.ns, p.UT, p.nt, p.tw_t, p.L, p.nbins))));
+    }
+    prof_end(p, st);
+    p.launches[stage]++;
+    return cudaGetLastError();
 }
 
 cudaError_t set_time_kernel_attrs(int lp, int interp, int max_smem) {
