@@ -26,6 +26,9 @@ What it computes (paper sections and equations):
                 the FFT'd q columns (A-coefficients of eq. thli).
 * ``bpull``     the paper's velocity scan (Algorithm 2): data on a regular
                 offset grid pulled at the rings k = f' r^2 (B-coefficients).
+* ``pnmo``      the curvature range of Sec. 3.5: the sample count of eq. q3,
+                the uniform-slowness (non-uniform q) axis, and the partial
+                NMO of the data with its transpose.
 * ``checks``    independent evaluations used only to pin the oracle: the
                 physical-domain Riemann sum along the azimuth-dependent
                 hyperbolae (eq. Inverse, Sec. 5.1) and the time-domain
@@ -40,4 +43,4 @@ the soft threshold's piecewise form, ISTA monotonicity, KKT optimality and
 spike recovery.  Every function in this package is covered by at least one.
 """
 from .plan import OraclePlan, make_plan            # noqa: F401
-from . import ops, fista, checks, decon, pick, lineark, bpull   # noqa: F401
+from . import ops, fista, checks, decon, pick, lineark, bpull, pnmo   # noqa: F401

@@ -70,6 +70,8 @@ def bilinear(Dk, grid: Grid, x, y):
 
 def pull_grid(plan, grid: Grid, Dk, k: int, sigma_q: float = 2.0):
     """G[u][j] of step 3 at bin k."""
+    if plan.q_axis is not None:
+        raise ValueError("the pull scan needs a uniform q axis (FFT along q)")
     nos = lineark.grid_size(plan.nq, sigma_q)
     cq = plan.nq // 2
     qc = plan.q0 + cq * plan.dq

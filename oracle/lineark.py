@@ -38,6 +38,8 @@ def grid_size(nq: int, sigma_q: float) -> int:
 
 
 def _geometry(plan, sigma_q):
+    if plan.q_axis is not None:
+        raise ValueError("the k-interpolation needs a uniform q axis (FFT along q)")
     nos = grid_size(plan.nq, sigma_q)
     cq = plan.nq // 2
     n_l = (np.arange(plan.nq) - cq) % nos                 # padded index of sample l

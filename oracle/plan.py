@@ -4,7 +4,9 @@ Readings of the paper used here (each is listed with its reason in the
 design notes of the repository):
 
 * The curvature axis is uniform, q_l = q0 + l*dq (FFT along q, Sec. 3.4 and
-  eq. q1-q3 need uniform q).
+  eq. q1-q3 need uniform q), unless explicit values q_axis are given (for
+  instance a uniform slowness axis, q_l = p_l^2): the slice step is then the
+  same sum over the non-uniform q_l (a type-3 DFT along q).
 * The model intercept axis is tau_i = i*dt for i < ntau, the data axis is
   t_i = i*dt for i < nt.
 * Stretched time s = t^2 (Sec. 3.1, eq. Inverse2) is sampled as
@@ -61,6 +63,7 @@ class OraclePlan:
     j1: np.ndarray
     w0: np.ndarray
     w1: np.ndarray
+    q_axis: np.ndarray | None = None   # explicit curvature values (non-uniform)
 
     @property
     def ntr(self) -> int:
@@ -72,7 +75,9 @@ class OraclePlan:
 
     @property
     def q(self) -> np.ndarray:
-        """Curvature axis q_l = q0 + l*dq."""
+        """Curvature axis: q_l = q0 + l*dq, or the explicit values."""
+        if self.q_axis is not None:
+            return self.q_axis
         return self.q0 + self.dq * np.arange(self.nq)
 
     @property
@@ -113,17 +118,24 @@ def azimuth_bins(hx, hy, ntheta):
 
 
 def make_plan(nt, dt, ntau, nq, q0, dq, ntheta, hx, hy, *, sigma_t=2.0,
-              fmax=0.0, interp="keys", r2max=None) -> OraclePlan:
+              fmax=0.0, interp="keys", r2max=None, q_axis=None) -> OraclePlan:
     """Stretched-time sampling plan (Sec. 3.4, step 1 and 2 of Algorithms 1
     and 2) and per-trace geometry.  r2max overrides the largest squared
     offset (a batch of cubes shares one time plan built from the batch-wide
-    maximum)."""
+    maximum).  q_axis: explicit curvature values (nq of them; q0 and dq are
+    then ignored)."""
     if interp not in ("keys", "linear"):
         raise ValueError("interp must be 'keys' or 'linear'")
     r2, th, j0, j1, w0, w1 = azimuth_bins(hx, hy, ntheta)
     tmax = (nt - 1) * dt
     r2m = float(np.max(r2)) if r2max is None else float(r2max)
-    qabs = max(abs(q0), abs(q0 + (nq - 1) * dq))
+    if q_axis is not None:
+        q_axis = np.array(q_axis, dtype=np.float64)
+        if q_axis.ndim != 1 or q_axis.size != nq or not np.all(np.isfinite(q_axis)):
+            raise ValueError("q_axis must hold nq finite values")
+        qabs = float(np.max(np.abs(q_axis)))
+    else:
+        qabs = max(abs(q0), abs(q0 + (nq - 1) * dq))
     rho = qabs * r2m / (tmax * tmax)
     nfft = next_pow2(int(math.ceil(sigma_t * nt * (1.0 + rho))))
     ns = int(math.floor((nfft - 2) / (1.0 + rho))) + 1
@@ -135,4 +147,4 @@ def make_plan(nt, dt, ntau, nq, q0, dq, ntheta, hx, hy, *, sigma_t=2.0,
                       ntheta=ntheta, hx=np.asarray(hx, np.float64),
                       hy=np.asarray(hy, np.float64), interp=interp, tmax=tmax,
                       rho=rho, nfft=nfft, ns=ns, ds=ds, kmax=kmax, r2=r2,
-                      theta=th, j0=j0, j1=j1, w0=w0, w1=w1)
+                      theta=th, j0=j0, j1=j1, w0=w0, w1=w1, q_axis=q_axis)
