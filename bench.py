@@ -12,12 +12,17 @@ of d and m are inside the timed region.  L2 is flushed (256 MB write)
 between timed steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--workload gather|batch512]
+                  [--workload gather|batch512|slowness|table1]
 
 --workload batch512 times the batched form instead: 512 CMP cubes (nt = 1001,
 fold 200-3000, offsets in a 3 km disc over a random 90-360 degree azimuth
 sector, 64 curvatures x 24 azimuths) in one autotuned plan, one step = one
 50-iteration FISTA solve of every cube with its own step and threshold.
+
+--workload slowness times the same gather and solve on a uniform slowness
+axis (100 slownesses 1/3500..1/1500 s/m, so the curvatures q = p^2 are not
+uniform): the slice step is the direct sum of the DFT along q (a type-3
+DFT), whose roofline is the special-function rate of the phases.
 
 Under torchrun each rank runs an independent replica on its own GPU (the
 path needs no communication); rank 0 prints one JSON line.
@@ -39,6 +44,9 @@ METRIC = ("AAHRT fwd+adj pairs/s and FISTA gathers/s on 1 GB300, %HBM roofline, 
 ITERS = 100
 WORKLOAD = ("paper-scale gather: nt=1001 dt=4ms, 2000 traces in a 3 km disc, "
             "100 q x 36 azimuths; one step = one 100-iteration FISTA solve")
+SLOW_WORKLOAD = ("paper-scale gather on a uniform slowness axis: nt=1001 dt=4ms, 2000 traces "
+                 "in a 3 km disc, 100 slownesses 1/3500..1/1500 s/m (non-uniform q) x 36 "
+                 "azimuths, direct-sum slice step; one step = one 100-iteration FISTA solve")
 BATCH_ITERS = 50
 BATCH_WORKLOAD = ("512 CMP cubes: nt=1001 dt=4ms, fold 200-3000 in 90-360 degree sectors "
                   "of a 3 km disc, 64 q x 24 azimuths, one autotuned plan; one step = one "
@@ -52,7 +60,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="gather", choices=["gather", "batch512", "table1"])
+    ap.add_argument("--workload", default="gather",
+                    choices=["gather", "batch512", "slowness", "table1"])
     return ap.parse_args()
 
 
@@ -201,6 +210,8 @@ def run_ours(args):
     from paper_2505_00387_gb300.plan import AahrtPlan
 
     batch = args.workload == "batch512"
+    slow = args.workload == "slowness"
+    qa = None
     if batch:
         cubes = syn.config3(seed=3 + rank)
         gp = AahrtPlan.batched(cubes, autotune=True)
@@ -208,7 +219,10 @@ def run_ours(args):
         iters, pairs_per_step = BATCH_ITERS, BATCH_ITERS * len(cubes)
     else:
         g = syn.config1(seed=1 + rank)
-        gp = AahrtPlan(**g.geom_kwargs())
+        if slow:
+            from paper_2505_00387_gb300.plan import q_axis_slowness
+            qa = q_axis_slowness(syn.P_MIN, syn.P_MAX, g.nq)
+        gp = AahrtPlan(**g.geom_kwargs(), q_axis=qa)
         d_np = g.d.astype(np.float32).ravel()
         iters, pairs_per_step = ITERS, ITERS
     info = gp.info
@@ -321,11 +335,16 @@ def run_ours(args):
                         ((info.xspec_len + info.yspec_len) * 8 / 1e9),
                   "parallelism": f"replicas x{world}"}
     else:
-        config = {"workload": WORKLOAD, "nt": g.nt, "dt": g.dt, "ntr": g.ntr, "nq": g.nq,
-                  "ntheta": g.ntheta, "fista_iters_per_step": iters, "nfft": info.nfft,
-                  "nbins": info.nbins, "spread_width": info.spread_width,
+        config = {"workload": SLOW_WORKLOAD if slow else WORKLOAD, "nt": g.nt, "dt": g.dt,
+                  "ntr": g.ntr, "nq": g.nq, "ntheta": g.ntheta, "fista_iters_per_step": iters,
+                  "nfft": info.nfft, "nbins": info.nbins,
                   "l2": "flushed between timed steps (256 MB write)",
                   "parallelism": f"replicas x{world}"}
+        if slow:
+            config["slice_step"] = "direct sum (type-3 DFT along q)"
+            config["theta_group"] = info.theta_group
+        else:
+            config["spread_width"] = info.spread_width
     sb = launch_bytes(info, st_n, args.steps * iters)
     names = L.STAGE_NAMES
     per_launch = [st_ms[i] / st_n[i] if st_n[i] else 0.0 for i in range(L.AAHRT_NSTAGES)]
@@ -338,7 +357,9 @@ def run_ours(args):
     kernel_names = ["r2c_kernel", "slice_fwd_kernel",
                     "c2r_r2c_kernel" if fused else "c2r_kernel", "r2c_kernel",
                     "slice_adj_kernel", "c2r_r2c_kernel" if fused else "c2r_kernel"]
-    tr = None if batch else traffic_record(names[top])
+    if slow:
+        kernel_names[1], kernel_names[4] = "direct_fwd_kernel", "direct_adj_kernel"
+    tr = None if (batch or slow) else traffic_record(names[top])
     line = {
         "metric": METRIC,
         "value": round(value, 3),
@@ -377,15 +398,33 @@ def run_ours(args):
                    for i in range(L.AAHRT_NSTAGES) if st_n[i]},
         "clocks": clocks,
     }
+    if slow and top in (1, 4):
+        # the direct sum is bound by the phases' sine/cosine pairs: one per
+        # (bin, trace, curvature) and launch; peak = SMs x 16 special-function
+        # results per clock / 2 (sine and cosine) x the maximum SM clock
+        props = torch.cuda.get_device_properties(dev)
+        mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+        peak_ph = props.multi_processor_count * 8 * mhz * 1e6 / 1e9
+        phases = info.nbins * g.ntr * g.nq
+        ach = phases / (per_launch[top] * 1e-3) / 1e9
+        line["roofline"] = {"bound": "alu", "achieved": round(ach, 1),
+                            "peak": round(peak_ph, 1), "unit": "Gphase/s",
+                            "frac": round(ach / peak_ph, 4), "traffic": tr,
+                            "kernel": kernel_names[top], "stage": names[top],
+                            "phases_per_launch": phases,
+                            "bytes_per_launch": sb[top],
+                            "avg_launch_ms": round(per_launch[top], 5),
+                            "peak_source": "derived: %d SMs x 8 sincos/clk x %.0f MHz" %
+                                           (props.multi_processor_count, mhz)}
     if world == 1 and not args.no_cpu_baseline:
         if batch:
             line["cpu_baseline"], line["err_vs_fp64"] = cpu_baseline_batch(cubes, gp, d, dev)
         else:
-            line["cpu_baseline"], line["err_vs_fp64"] = cpu_baseline(g, gp, d, dev)
+            line["cpu_baseline"], line["err_vs_fp64"] = cpu_baseline(g, gp, d, dev, q_axis=qa)
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(g, gp, d_dev, dev, pairs=2):
+def cpu_baseline(g, gp, d_dev, dev, pairs=2, q_axis=None):
     """The FP64 checker timed on this host's cores on a bounded sample of the
     same workload (`pairs` forward+adjoint pairs of the full gather), and
     the GPU path's relative error against those FP64 results."""
@@ -395,7 +434,7 @@ def cpu_baseline(g, gp, d_dev, dev, pairs=2):
     import oracle
     from oracle import ops
 
-    p = oracle.make_plan(**g.geom_kwargs())
+    p = oracle.make_plan(**g.geom_kwargs(), q_axis=q_axis)
     rng = np.random.default_rng(123)
     mr = rng.standard_normal((g.ntau, g.nq, g.ntheta)).astype(np.float32).astype(np.float64)
     ops.slice_forward(p.subset_traces([0]), np.zeros((p.nbins, p.nq, p.ntheta), complex))

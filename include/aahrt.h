@@ -18,7 +18,8 @@
  * (eq. ISTA with the shrinkage of eq. soft), optionally with FISTA momentum.
  *
  * Discretisation (fixed at plan creation):
- *   tau_i = i*dt (i < ntau), t_i = i*dt (i < nt), q_l = q0 + l*dq (l < nq),
+ *   tau_i = i*dt (i < ntau), t_i = i*dt (i < nt), q_l = q0 + l*dq (l < nq;
+ *   or explicit values, opts.q_axis),
  *   theta_j = j*pi/ntheta (j < ntheta); a trace at offset (hx, hy) has
  *   r^2 = hx^2 + hy^2 and axial azimuth atan2(hy, hx) mod pi, and reads the
  *   two neighbouring azimuth slices with linear weights (theta factors of
@@ -90,8 +91,14 @@ extern "C" {
  *   between the two neighbouring k samples, no deapodisation (second-order
  *   in the k spacing: about 30 % error at sigma_q = 1, 8 % at 2 on smooth
  *   events; see the design notes).  The adjoint is its exact transpose. */
+/* AAHRT_SLICE_DIRECT: the DFT along q summed directly at k_q = f_k r^2
+ *   with exact phases (64-bit fixed-point phase arguments, FP32 sums on the
+ *   CUDA cores; about 1e-6 relative): O(nq) work per bin and trace instead
+ *   of the spreading kernel's O(W), for any curvature axis.  Plans with an
+ *   explicit opts.q_axis always use it (slice_interp 0 or 2). */
 #define AAHRT_SLICE_SPREAD 0
 #define AAHRT_SLICE_LINEAR_K 1
+#define AAHRT_SLICE_DIRECT 2
 
 #define AAHRT_PRECISION_FP32 0
 #define AAHRT_PRECISION_SPLIT_BF16 1
@@ -101,8 +108,8 @@ typedef struct aahrt_plan aahrt_plan;
 /* Axes and trace geometry of one CMP cube.  hx, hy: host arrays of ntr
  * offsets in metres, copied at plan creation (the caller keeps ownership).
  * dt in seconds, q0 and dq in s^2/m^2.  Requires nt >= 4, ntau >= 4,
- * nq >= 1, ntheta >= 1, ntr >= 1, dt > 0, dq > 0 when nq > 1, and at least
- * one nonzero offset. */
+ * nq >= 1, ntheta >= 1, ntr >= 1, dt > 0, dq > 0 when nq > 1 (q0 and dq are
+ * not read when opts.q_axis is given), and at least one nonzero offset. */
 typedef struct {
     int nt;
     double dt;
@@ -136,6 +143,15 @@ typedef struct {
     double sigma_q;     /* q grid oversampling: the grid has max(16,
                            next_pow2(ceil(sigma_q nq))) points; 0 = 2; the
                            spreading kernel needs >= 1.25 nq points */
+    const double *q_axis;  /* NULL: the uniform axis q_l = q0 + l dq of the
+                           geometry.  Else a host array of nq finite
+                           curvatures in s^2/m^2 (any order, copied; q0 and
+                           dq are then ignored), for instance the uniform-
+                           slowness axis of aahrt_q_axis_slowness: the slice
+                           step is the direct sum over these q_l (a type-3
+                           DFT along q; AAHRT_SLICE_DIRECT, or the tensor-core
+                           contraction).  Not available with
+                           AAHRT_SLICE_LINEAR_K or the pull scan. */
 } aahrt_opts;
 
 /* What a plan chose (filled by aahrt_plan_query). */
@@ -160,6 +176,7 @@ typedef struct {
     int autotuned;           /* 1 if the autotuner chose the tiles above */
     double tune_ms;          /* autotuner: best forward+adjoint time of its trial batch */
     int precision;           /* AAHRT_PRECISION_* of the slice step */
+    int slice_interp;        /* AAHRT_SLICE_* the FP32 slice step runs */
 } aahrt_plan_info;
 
 /* Create a plan on the current CUDA device: validates the geometry,
@@ -181,8 +198,8 @@ int aahrt_plan_create(aahrt_plan **out, const aahrt_geom *geom,
                       const aahrt_opts *opts);
 
 /* Create one plan for ncube independent CMP cubes of different fold and
- * azimuth coverage.  All cubes must share nt, dt, ntau, nq, q0, dq and
- * ntheta; they share one stretched-time sampling built from the largest
+ * azimuth coverage.  All cubes must share nt, dt, ntau, nq, q0, dq (unless
+ * opts.q_axis gives the axis) and ntheta; they share one stretched-time sampling built from the largest
  * offset of the whole batch.  m holds the cubes' models back to back,
  * d their data back to back (cube c has geoms[c].ntr traces). */
 int aahrt_plan_create_batched(aahrt_plan **out, int ncube,
@@ -337,6 +354,39 @@ int aahrt_fista_vjp(aahrt_plan *plan, const float *d, const float *m_bar,
  * dq = (pmax^2 - pmin^2)/(nq - 1) (curvature is squared slowness, Sec. 2). */
 int aahrt_q_from_slowness(double pmin, double pmax, int nq, double *q0,
                           double *dq);
+
+/* Uniform-slowness curvature axis (non-uniform in q): q[l] = p_l^2 with
+ * p_l = pmin + l (pmax - pmin)/(nq - 1) (p_0 = pmin when nq = 1), for
+ * opts.q_axis.  q: host array of nq doubles.  Requires finite pmin, pmax
+ * and nq >= 1. */
+int aahrt_q_axis_slowness(double pmin, double pmax, int nq, double *q);
+
+/* Curvature sampling bound of Sec. 3.5 (eqs. q1-q3).  k_q = f' r^2 is never
+ * negative, so a uniform q step dq reads it without aliasing over a whole
+ * period 1/dq when dq <= 1/(fmax r2max); a range of width span (2 q_max for
+ * the paper's axis [-q_max, q_max], eq. q3) then needs
+ *   *nq = max(1, ceil(span fmax r2max))
+ * samples.  fmax: highest stretched-time frequency inverted (1/s^2; a plan's
+ * is (nbins - 1)/(nfft ds)), r2max: largest squared offset (m^2).  A partial
+ * NMO by q_ref = (q_a + q_b)/2 (aahrt_partial_nmo) turns a range [q_a, q_b]
+ * into one of width q_b - q_a centred on zero.  Requires span, fmax,
+ * r2max >= 0 and finite, and a count below 2^31. */
+int aahrt_nq_required(double span, double fmax, double r2max, int *nq);
+
+/* Partial NMO of the data by a reference curvature q_ref (Sec. 3.5): in
+ * stretched time s = t^2 every trace is shifted by -q_ref r^2, which moves a
+ * hyperbola of curvature q to q - q_ref; it is applied on the time axis in
+ * one resampling with the plan's interpolation kernel:
+ *   out(t_i, h) = sum_taps c(u - n) in(t_n, h),  u = sqrt(t_i^2 + q_ref r_h^2)/dt,
+ * zero where t_i^2 + q_ref r_h^2 < 0 and taps outside [0, nt) taken as 0.
+ * transpose = 1 applies the exact transpose of that map instead (a gather
+ * over the output samples whose taps reach each input sample; no atomics).
+ * The inverse of the map is the map with -q_ref (up to interpolation and the
+ * muted zone).  in and out: data_len floats of device memory in the plan's
+ * data layout (every trace of every cube or gather), 16-byte aligned, not
+ * overlapping.  q_ref must be finite.  Stream-ordered. */
+int aahrt_partial_nmo(aahrt_plan *plan, const float *in, float *out, double q_ref,
+                      int transpose, void *stream);
 
 /* Per-stage device time.  While profiling is on, every stage launch of the
  * plan is bracketed by CUDA events on its stream and, at

@@ -22,6 +22,7 @@ AAHRT_INTERP_KEYS = 0
 AAHRT_INTERP_LINEAR = 1
 AAHRT_SLICE_SPREAD = 0
 AAHRT_SLICE_LINEAR_K = 1
+AAHRT_SLICE_DIRECT = 2
 AAHRT_PRECISION_FP32 = 0
 AAHRT_PRECISION_SPLIT_BF16 = 1
 AAHRT_NSTAGES = 7
@@ -39,7 +40,8 @@ class aahrt_opts(ctypes.Structure):
     _fields_ = [("interp_kind", c_int), ("spread_width", c_int), ("theta_group", c_int),
                 ("ngather", c_int), ("sigma_t", c_double), ("fmax", c_double),
                 ("time_pairs", c_int), ("autotune", c_int), ("precision", c_int),
-                ("slice_interp", c_int), ("sigma_q", c_double)]
+                ("slice_interp", c_int), ("sigma_q", c_double),
+                ("q_axis", POINTER(c_double))]
 
 
 class aahrt_plan_info(ctypes.Structure):
@@ -49,7 +51,7 @@ class aahrt_plan_info(ctypes.Structure):
                 ("model_len", c_longlong), ("data_len", c_longlong),
                 ("xspec_len", c_longlong), ("yspec_len", c_longlong),
                 ("workspace_bytes", c_longlong), ("time_pairs", c_int), ("autotuned", c_int),
-                ("tune_ms", c_double), ("precision", c_int)]
+                ("tune_ms", c_double), ("precision", c_int), ("slice_interp", c_int)]
 
 
 class aahrt_grid(ctypes.Structure):
@@ -97,6 +99,9 @@ _SIGS = {
     "aahrt_velocity_scan_grid": (c_int, [c_void_p, POINTER(aahrt_grid), c_void_p, c_void_p,
                                          c_void_p]),
     "aahrt_forward_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "aahrt_q_axis_slowness": (c_int, [c_double, c_double, c_int, POINTER(c_double)]),
+    "aahrt_nq_required": (c_int, [c_double, c_double, c_double, POINTER(c_int)]),
+    "aahrt_partial_nmo": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_int, c_void_p]),
     "aahrt_q_from_slowness": (c_int, [c_double, c_double, c_int, POINTER(c_double),
                                       POINTER(c_double)]),
     "aahrt_plan_set_profiling": (c_int, [c_void_p, c_int]),
@@ -204,6 +209,24 @@ def aahrt_q_from_slowness(pmin: float, pmax: float, nq: int):
     check(load().aahrt_q_from_slowness(pmin, pmax, nq, ctypes.byref(q0), ctypes.byref(dq)),
           "aahrt_q_from_slowness")
     return q0.value, dq.value
+
+
+def aahrt_q_axis_slowness(pmin: float, pmax: float, nq: int):
+    q = (c_double * max(1, int(nq)))()
+    check(load().aahrt_q_axis_slowness(pmin, pmax, int(nq), q), "aahrt_q_axis_slowness")
+    return [q[i] for i in range(int(nq))]
+
+
+def aahrt_nq_required(span: float, fmax: float, r2max: float) -> int:
+    n = c_int()
+    check(load().aahrt_nq_required(span, fmax, r2max, ctypes.byref(n)), "aahrt_nq_required")
+    return n.value
+
+
+def aahrt_partial_nmo(h, in_ptr: int, out_ptr: int, q_ref: float, transpose: bool = False,
+                      stream: int = 0):
+    check(load().aahrt_partial_nmo(h, c_void_p(in_ptr), c_void_p(out_ptr), c_double(q_ref),
+                                   int(bool(transpose)), c_void_p(stream)), "aahrt_partial_nmo")
 
 
 def aahrt_plan_set_profiling(h, on: bool):

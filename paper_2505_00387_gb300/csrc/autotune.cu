@@ -144,7 +144,11 @@ int autotune_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
     Plan *ref = nullptr;
     aahrt_opts o = base;
     const bool lineark = base.slice_interp == AAHRT_SLICE_LINEAR_K;
-    if (!lineark) o.spread_width = kMaxW;
+    // the direct sum (explicit q axes) and the tensor-core contraction have
+    // no spreading kernel to size
+    const bool no_width = base.slice_interp == AAHRT_SLICE_DIRECT || base.q_axis != nullptr ||
+                          base.precision == AAHRT_PRECISION_SPLIT_BF16;
+    if (!lineark && !no_width) o.spread_width = kMaxW;
     if ((rc = make(o, &ref))) return rc;
     const long long nm = ref->model_len, nd = ref->data_len;
     DevBuf bm, bd, bd2, bg, bacc;
@@ -164,7 +168,7 @@ int autotune_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
 
     // spreading width: smallest with measured relative error <= 2e-6
     int W = base.spread_width;
-    if (W == 0 && !lineark) {
+    if (W == 0 && !lineark && !no_width) {
         W = kMaxW;
         for (int w = kMinW + 1; w < kMaxW; ++w) {
             Plan *pw = nullptr;

@@ -118,6 +118,9 @@ extern "C" int aahrt_velocity_scan_grid(aahrt_plan *plan, const aahrt_grid *grid
         return set_error(AAHRT_ERR_UNSUPPORTED, "the grid scan needs a single-gather FP32 plan");
     if (p.ntau != p.nt || p.nq < 2)
         return set_error(AAHRT_ERR_UNSUPPORTED, "the grid scan needs ntau == nt and nq >= 2");
+    if (p.qexplicit)
+        return set_error(AAHRT_ERR_UNSUPPORTED, "the grid scan needs a uniform q axis (FFT "
+                         "along q)");
     if (grid->nx < 1 || grid->ny < 1 || (long long)grid->nx * grid->ny != p.ntr[0] ||
         !(grid->dx > 0.0) || !(grid->dy > 0.0) || !std::isfinite(grid->x0) ||
         !std::isfinite(grid->y0))
@@ -125,15 +128,22 @@ extern "C" int aahrt_velocity_scan_grid(aahrt_plan *plan, const aahrt_grid *grid
                          "dx, dy > 0", p.ntr[0]);
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e;
-    static bool attr_set = false;     // function attribute, process-wide
-    if (!attr_set) {
-        int max_smem = 0;
-        if ((e = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin,
+    static int max_smem = 0;          // function attribute, process-wide
+    if (!max_smem) {
+        int mx = 0;
+        if ((e = cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin,
                                         p.device)) ||
-            (e = raise_smem_limit(pull_kernel, max_smem)))
+            (e = raise_smem_limit(pull_kernel, mx)))
             return cuda_fail(e, "pull kernel attributes");
-        attr_set = true;
+        cudaFuncAttributes at;
+        if ((e = cudaFuncGetAttributes(&at, pull_kernel))) return cuda_fail(e, "pull kernel attributes");
+        max_smem = mx - (int)at.sharedSizeBytes;
     }
+    // one group's split q grid (re and im planes of every owned slice)
+    const size_t smem = (size_t)p.tgroup * ld_split(p.nos) * 2 * sizeof(float);
+    if ((int)smem > max_smem)
+        return set_error(AAHRT_ERR_UNSUPPORTED, "the grid scan's q grids (%zu bytes) exceed "
+                         "shared memory; lower theta_group", smem);
     if ((e = launch_stretch_data(p, d, p.Y, st))) return cuda_fail(e, "stretch+FFT launch");
     PullArgs a;
     a.D = p.Y;
@@ -160,7 +170,7 @@ extern "C" int aahrt_velocity_scan_grid(aahrt_plan *plan, const aahrt_grid *grid
     a.kscale = 1.0 / (p.nfft * p.ds);
     a.scale = (float)(1.0 / p.nfft);
     prof_begin(p, 4, st);
-    pull_kernel<<<p.nbins * p.ngroup, 256, p.smem_sadj, st>>>(a, p.X);
+    pull_kernel<<<p.nbins * p.ngroup, 256, smem, st>>>(a, p.X);
     prof_end(p, st);
     p.launches[4]++;
     if ((e = cudaGetLastError())) return cuda_fail(e, "pull launch");

@@ -45,6 +45,16 @@ struct SliceGroup {
     long long ss_off;   // offset of the cube's slice-start table (ntheta + 1 ints)
 };
 
+// Data block of the partial NMO: nt rows of ld floats starting at float
+// offset off; column c of a row belongs to trace r0 + c / rep (rep = gathers
+// stored fastest, else 1).
+struct PnBlock {
+    long long off;
+    long long r0;
+    int ld;
+    int rep;
+};
+
 // Column group of the time-axis kernels (at most 2*pairs columns).
 struct ColGroup {
     long long real_off;  // float offset of the group's first column in the
@@ -152,7 +162,21 @@ struct Plan {
     long long *dseg = nullptr;     // data offsets of the cubes (ncube + 1 entries)
     // tensor-core direct contraction (precision 1): gathers stored fastest
     int precision = 0;
-    int slice_interp = 0;          // AAHRT_SLICE_SPREAD or AAHRT_SLICE_LINEAR_K
+    int slice_interp = 0;          // AAHRT_SLICE_SPREAD, _LINEAR_K or _DIRECT
+    // curvature axis: q_l = qc + qn[l] * qeps exactly (qn integer); the
+    // uniform axis has qc = q0 + cq dq, qeps = dq, qn[l] = l - cq
+    bool qexplicit = false;        // opts.q_axis given (non-uniform q)
+    std::vector<double> qaxis;     // q_l (host)
+    double qc = 0, qeps = 0;
+    long long *qn = nullptr;       // device [nq]
+    double *qv = nullptr;          // device [nq], q_l
+    int direct_chunk = 0;          // traces the direct adjoint stages per pass
+    // partial NMO: data blocks and per-trace r^2 / dt^2
+    PnBlock *pn_blk = nullptr;
+    int pn_nblk = 0, pn_ldmax = 0;
+    double *pn_rho = nullptr;      // [traces of every distinct geometry]
+    float2 *pn_c = nullptr;        // per trace q_ref r^2/dt^2 as (hi, lo)
+    long long pn_ntr = 0;
     int tc_gp = 0;                 // gathers padded to a multiple of 8
     int4 *tc_tiles = nullptr;      // forward row tiles {slice, first, end, 0}
     int tc_ntiles = 0;
@@ -207,6 +231,12 @@ cudaError_t launch_c2r_r2c(Plan &p, bool model_side, float2 *spec, const float *
                            FistaArgs fa, cudaStream_t st);
 cudaError_t launch_slice_tc(Plan &p, bool adjoint, const float2 *in, float2 *out,
                             cudaStream_t st, int *counter);
+// direct sum of the DFT along q (any curvature axis)
+cudaError_t launch_slice_direct(Plan &p, bool adjoint, const float2 *in, float2 *out,
+                                cudaStream_t st, int *counter);
+cudaError_t configure_direct_kernels(Plan &p, int num_sms, int max_smem);
+size_t direct_smem_fwd(int tgroup, int extra, int nq);
+size_t direct_smem_adj(int tgroup, int nq, int chunk);
 cudaError_t configure_tc_kernels(Plan &p, int num_sms, int max_smem);
 // time convolution of the data columns with the plan's wavelet: mode 0 out = W in,
 // 1 out = aux - W in, 2 out = W^T in

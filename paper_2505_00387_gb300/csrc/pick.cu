@@ -14,7 +14,7 @@ namespace aahrt {
 // fastest in tensor-core plans, else 1); out: [ncube][ntau][inner]
 __global__ void pick_kernel(const float *__restrict__ m, float *__restrict__ qhat,
                             float *__restrict__ wsum, long long nout, int ntau, int nq,
-                            int inner, double q0, double dq) {
+                            int inner, const double *__restrict__ q) {
     for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < nout;
          o += (long long)gridDim.x * blockDim.x) {
         const long long row = o / inner;          // cube * ntau + tau
@@ -23,7 +23,7 @@ __global__ void pick_kernel(const float *__restrict__ m, float *__restrict__ qha
         double num = 0.0, den = 0.0;
         for (int l = 0; l < nq; ++l) {
             const double a = fabs((double)__ldg(col + (long long)l * inner));
-            num += (q0 + l * dq) * a;
+            num += __ldg(q + l) * a;
             den += a;
         }
         qhat[o] = den > 0.0 ? (float)(num / den) : 0.f;
@@ -49,7 +49,7 @@ extern "C" int aahrt_pick_velocity(aahrt_plan *plan, const float *m, float *q_ha
     const long long nout = (long long)blocks * p.ntau * inner;
     const int grid = (int)std::min<long long>((nout + 255) / 256, 152 * 16);
     pick_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(m, q_hat, weight, nout, p.ntau, p.nq,
-                                                         inner, p.q0, p.dq);
+                                                         inner, p.qv);
     p.launches[6]++;
     cudaError_t e = cudaGetLastError();
     return e ? cuda_fail(e, "pick launch") : AAHRT_OK;

@@ -143,8 +143,8 @@ static CubeGeo bin_cube(const Plan &p, const double *hx, const double *hy, int n
         if (j < 0) j = 0;
         if (j >= p.ntheta) j = p.ntheta - 1;
         TraceGeo t;
-        t.A = to_fixed64((p.q0 + p.cq * p.dq) * r2 * scale);
-        t.B = to_fixed64(p.dq * r2 * scale);
+        t.A = to_fixed64(p.qc * r2 * scale);
+        t.B = to_fixed64(p.qeps * r2 * scale);
         t.w0 = (float)(1.0 - fr);
         t.w1 = (float)fr;
         t.j0 = j;
@@ -183,14 +183,15 @@ void free_plan(Plan *p) {
                     p->cg_model, p->cg_data, p->cg_model_blk, p->cg_data_blk, p->posS,
                     p->posU, p->rngST, p->rngUT, p->X, p->Y, p->z, p->r, p->v, p->scal,
                     p->stage_m, p->stage_d, p->zb, p->mb, p->rb, p->db, p->vjp_ws,
-                    p->cube_gt, p->cube_acc, p->dseg, p->tc_tiles, p->wav, p->wtmp};
+                    p->cube_gt, p->cube_acc, p->dseg, p->tc_tiles, p->wav, p->wtmp,
+                    p->qn, p->qv, p->pn_blk, p->pn_rho, p->pn_c};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     cudaSetDevice(cur);
     delete p;
 }
 
-static int validate_geom(const aahrt_geom *g, int idx) {
+static int validate_geom(const aahrt_geom *g, int idx, bool q_explicit) {
     if (!g) return set_error(AAHRT_ERR_INVALID_ARG, "geometry %d is NULL", idx);
     if (g->nt < 4 || g->ntau < 4)
         return set_error(AAHRT_ERR_INVALID_ARG, "geometry %d: nt and ntau must be >= 4", idx);
@@ -198,7 +199,8 @@ static int validate_geom(const aahrt_geom *g, int idx) {
         return set_error(AAHRT_ERR_INVALID_ARG, "geometry %d: nq, ntheta, ntr must be >= 1", idx);
     if (!(g->dt > 0.0) || !std::isfinite(g->dt))
         return set_error(AAHRT_ERR_INVALID_ARG, "geometry %d: dt must be > 0", idx);
-    if (!std::isfinite(g->q0) || !std::isfinite(g->dq) || (g->nq > 1 && !(g->dq > 0.0)))
+    if (!q_explicit &&
+        (!std::isfinite(g->q0) || !std::isfinite(g->dq) || (g->nq > 1 && !(g->dq > 0.0))))
         return set_error(AAHRT_ERR_INVALID_ARG, "geometry %d: q0/dq invalid", idx);
     if (!g->hx || !g->hy)
         return set_error(AAHRT_ERR_INVALID_ARG, "geometry %d: hx/hy are NULL", idx);
@@ -221,14 +223,15 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
     std::memset(&opts, 0, sizeof opts);
     if (opts_in) opts = *opts_in;
     for (int c = 0; c < ndist; ++c) {
-        int rc = validate_geom(geoms + c, c);
+        int rc = validate_geom(geoms + c, c, opts.q_axis != nullptr);
         if (rc) return rc;
     }
     const aahrt_geom &g0 = geoms[0];
     for (int c = 1; c < ndist; ++c) {
         const aahrt_geom &g = geoms[c];
-        if (g.nt != g0.nt || g.dt != g0.dt || g.ntau != g0.ntau || g.nq != g0.nq ||
-            g.q0 != g0.q0 || g.dq != g0.dq || g.ntheta != g0.ntheta)
+        const bool qdiff = opts.q_axis == nullptr && (g.q0 != g0.q0 || g.dq != g0.dq);
+        if (g.nt != g0.nt || g.dt != g0.dt || g.ntau != g0.ntau || g.nq != g0.nq || qdiff ||
+            g.ntheta != g0.ntheta)
             return set_error(AAHRT_ERR_INVALID_ARG,
                              "cube %d: axes differ from cube 0 (nt, dt, ntau, nq, q0, dq, "
                              "ntheta must be shared)", c);
@@ -237,8 +240,18 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
         return set_error(AAHRT_ERR_INVALID_ARG, "interp_kind must be 0 or 1");
     int W = opts.spread_width;
     const bool lineark = opts.slice_interp == AAHRT_SLICE_LINEAR_K;
-    if (opts.slice_interp != AAHRT_SLICE_SPREAD && !lineark)
-        return set_error(AAHRT_ERR_INVALID_ARG, "slice_interp must be 0 or 1");
+    if (opts.slice_interp != AAHRT_SLICE_SPREAD && !lineark &&
+        opts.slice_interp != AAHRT_SLICE_DIRECT)
+        return set_error(AAHRT_ERR_INVALID_ARG, "slice_interp must be 0, 1 or 2");
+    const bool qexplicit = opts.q_axis != nullptr;
+    if (qexplicit) {
+        for (int l = 0; l < g0.nq; ++l)
+            if (!std::isfinite(opts.q_axis[l]))
+                return set_error(AAHRT_ERR_NONFINITE, "q_axis[%d] is not finite", l);
+        if (lineark)
+            return set_error(AAHRT_ERR_UNSUPPORTED, "the k-interpolation needs a uniform q "
+                             "axis (FFT along q)");
+    }
     if (lineark) {
         if (W != 0 && W != 2)
             return set_error(AAHRT_ERR_INVALID_ARG, "linear k-interpolation has 2 taps");
@@ -280,8 +293,8 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
     p->dt = g0.dt;
     p->ntau = g0.ntau;
     p->nq = g0.nq;
-    p->q0 = g0.q0;
-    p->dq = g0.nq > 1 ? g0.dq : 0.0;
+    p->q0 = qexplicit ? 0.0 : g0.q0;
+    p->dq = (qexplicit || g0.nq < 2) ? 0.0 : g0.dq;
     p->ntheta = g0.ntheta;
     p->interp = opts.interp_kind;
     p->sigma_t = opts.sigma_t > 0.0 ? opts.sigma_t : 2.0;
@@ -302,7 +315,15 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
     }
     int rc_fail = AAHRT_OK;
     p->tmax = (p->nt - 1) * p->dt;
-    const double qabs = std::max(std::fabs(p->q0), std::fabs(p->q0 + (p->nq - 1) * p->dq));
+    if (qexplicit) {
+        p->qexplicit = true;
+        p->qaxis.assign(opts.q_axis, opts.q_axis + p->nq);
+    } else {
+        p->qaxis.resize(p->nq);
+        for (int l = 0; l < p->nq; ++l) p->qaxis[l] = p->q0 + l * p->dq;
+    }
+    double qabs = 0.0;
+    for (int l = 0; l < p->nq; ++l) qabs = std::max(qabs, std::fabs(p->qaxis[l]));
     p->rho = qabs * r2max / (p->tmax * p->tmax);
     const double want = std::ceil(p->sigma_t * p->nt * (1.0 + p->rho));
     if (!(want <= 16384.0)) {
@@ -328,9 +349,27 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
     p->nos = (int)std::max(16LL, next_pow2((long long)std::ceil(sq * p->nq - 1e-9)));
     p->Lq = ilog2(p->nos);
     p->cq = p->nq / 2;
-    p->slice_interp = opts.slice_interp;
+    p->slice_interp = (qexplicit && !tc) ? AAHRT_SLICE_DIRECT : opts.slice_interp;
+    if (tc) p->slice_interp = AAHRT_SLICE_SPREAD;
+    const bool direct = p->slice_interp == AAHRT_SLICE_DIRECT;
+    // the curvature axis as q_c + n_l eps with integers n_l: the uniform axis
+    // centred at l = cq, or an explicit one centred on its range with a
+    // quantum eps of 2^-30 of its half-width (n_l exact to half a quantum)
+    std::vector<long long> qn(p->nq);
+    if (!qexplicit) {
+        p->qc = p->q0 + p->cq * p->dq;
+        p->qeps = p->dq;
+        for (int l = 0; l < p->nq; ++l) qn[l] = l - p->cq;
+    } else {
+        const auto mm = std::minmax_element(p->qaxis.begin(), p->qaxis.end());
+        p->qc = 0.5 * (*mm.first + *mm.second);
+        const double half = 0.5 * (*mm.second - *mm.first);
+        p->qeps = half > 0.0 ? std::ldexp(half, -30) : 1.0;
+        for (int l = 0; l < p->nq; ++l)
+            qn[l] = std::llround((p->qaxis[l] - p->qc) / p->qeps);
+    }
     const double sigma_q = (double)p->nos / p->nq;
-    if (!lineark && sigma_q < 1.25) {
+    if (!lineark && !direct && !tc && sigma_q < 1.25) {
         rc_fail = set_error(AAHRT_ERR_UNSUPPORTED, "the spreading kernel needs a q grid of at "
                             "least 1.25 nq points (sigma_q)");
         free_plan(p);
@@ -354,6 +393,14 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
                              sizeof(float2);
     if (opts.theta_group > 0) {
         p->tgroup = std::min(opts.theta_group, p->ntheta);
+    } else if (direct) {
+        // the forward stages nq x (slices + 1) values, the adjoint two planes
+        // of nq x slices accumulators beside its staged traces (32 bytes each)
+        const int by_fwd = (int)(64 * 1024 / ((size_t)p->nq * sizeof(float2))) - 1;
+        const int by_adj = (int)(48 * 1024 / (2 * (size_t)p->nq * sizeof(float2)));
+        const int t = std::max(1, std::min(by_fwd, by_adj));
+        const int ng = (p->ntheta + t - 1) / t;
+        p->tgroup = (p->ntheta + ng - 1) / ng;
     } else {
         const size_t budget = 72 * 1024;      // three blocks per SM
         if (p->ntheta * per_slice <= budget) {
@@ -573,6 +620,32 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
     AAHRT_TRY(upload(&p->posU, posU), "upload resamplers");
     AAHRT_TRY(upload(&p->rngST, rngST), "upload resamplers");
     AAHRT_TRY(upload(&p->rngUT, rngUT), "upload resamplers");
+    AAHRT_TRY(upload(&p->qn, qn), "upload curvature axis");
+    AAHRT_TRY(upload(&p->qv, p->qaxis), "upload curvature axis");
+    {   // partial NMO: data blocks and r^2/dt^2 of every trace of every geometry
+        std::vector<PnBlock> blk;
+        std::vector<double> rho;
+        std::vector<long long> r0(ndist);
+        for (int c = 0; c < ndist; ++c) {
+            r0[c] = (long long)rho.size();
+            for (int h = 0; h < geoms[c].ntr; ++h)
+                rho.push_back((geoms[c].hx[h] * geoms[c].hx[h] + geoms[c].hy[h] * geoms[c].hy[h]) /
+                              (p->dt * p->dt));
+        }
+        if (tc) {
+            blk.push_back(PnBlock{0, 0, geoms[0].ntr * G_tc, G_tc});
+        } else {
+            for (int c = 0; c < ncube; ++c)
+                blk.push_back(PnBlock{p->data_off[c], r0[ndist == 1 ? 0 : c], p->ntr[c], 1});
+        }
+        p->pn_nblk = (int)blk.size();
+        p->pn_ldmax = 0;
+        for (const PnBlock &b : blk) p->pn_ldmax = std::max(p->pn_ldmax, b.ld);
+        p->pn_ntr = (long long)rho.size();
+        AAHRT_TRY(upload(&p->pn_blk, blk), "upload data blocks");
+        AAHRT_TRY(upload(&p->pn_rho, rho), "upload offsets");
+        AAHRT_TRY(cudaMalloc((void **)&p->pn_c, rho.size() * sizeof(float2)), "alloc offsets");
+    }
     AAHRT_TRY(cudaMalloc((void **)&p->counters, 16 * sizeof(int)), "alloc counters");
     AAHRT_TRY(cudaMemset(p->counters, 0, 16 * sizeof(int)), "clear counters");
     p->S = DevResampler{p->posS, nullptr, p->ns, p->ns};
@@ -596,9 +669,20 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
     p->smem_fused_data = p->smem_r2c_data;
     const size_t smem_r2c = std::max(p->smem_r2c_model, p->smem_r2c_data);
     const size_t smem_c2r = std::max(p->smem_c2r_model, p->smem_c2r_data);
-    p->smem_sfwd = (size_t)(p->tgroup + (p->ngroup > 1 ? 1 : 0)) * ld_interleaved(p->nos) *
-                   sizeof(float2);
-    p->smem_sadj = (size_t)p->tgroup * ld_split(p->nos) * 2 * sizeof(float);
+    if (direct) {
+        int most = 32;
+        for (const SliceGroup &s : groups) most = std::max(most, s.f1 - s.f0 + s.e1 - s.e0);
+        const size_t base = direct_smem_adj(p->tgroup, p->nq, 0);
+        const size_t budget = 72 * 1024;
+        const int room = base < budget ? (int)((budget - base) / 32) : 0;
+        p->direct_chunk = std::max(64, std::min(most, room));
+        p->smem_sfwd = direct_smem_fwd(p->tgroup, p->ngroup > 1 ? 1 : 0, p->nq);
+        p->smem_sadj = direct_smem_adj(p->tgroup, p->nq, p->direct_chunk);
+    } else {
+        p->smem_sfwd = (size_t)(p->tgroup + (p->ngroup > 1 ? 1 : 0)) * ld_interleaved(p->nos) *
+                       sizeof(float2);
+        p->smem_sadj = (size_t)p->tgroup * ld_split(p->nos) * 2 * sizeof(float);
+    }
     int max_smem = 0;
     AAHRT_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin,
                                      p->device), "device query");
@@ -624,6 +708,8 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
         p->tc_ntiles = (int)tiles.size();
         AAHRT_TRY(upload(&p->tc_tiles, tiles), "upload row tiles");
         AAHRT_TRY(configure_tc_kernels(*p, num_sms, max_smem), "tensor-core kernel configuration");
+    } else if (direct) {
+        AAHRT_TRY(configure_direct_kernels(*p, num_sms, max_smem), "direct kernel configuration");
     } else {
         AAHRT_TRY(configure_slice_kernels(*p, num_sms, max_smem), "slice kernel configuration");
     }
@@ -654,6 +740,7 @@ void plan_info(const Plan &p, aahrt_plan_info *info) {
     info->autotuned = p.autotuned ? 1 : 0;
     info->tune_ms = p.tune_ms;
     info->precision = p.precision;
+    info->slice_interp = p.slice_interp;
 }
 
 // ----------------------------------------------------------- profiling

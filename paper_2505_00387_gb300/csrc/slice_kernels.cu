@@ -396,9 +396,10 @@ cudaError_t launch_slice(Plan &p, bool adjoint, const float2 *in, float2 *out,
     int *ctr = counter ? counter : p.counters + slot;
     cudaError_t e = cudaMemsetAsync(ctr, 0, sizeof(int), st);
     if (e) return e;
-    if (p.precision == 1) {
+    if (p.precision == 1 || p.slice_interp == AAHRT_SLICE_DIRECT) {
         prof_begin(p, stage, st);
-        e = launch_slice_tc(p, adjoint, in, out, st, ctr);
+        e = p.precision == 1 ? launch_slice_tc(p, adjoint, in, out, st, ctr)
+                             : launch_slice_direct(p, adjoint, in, out, st, ctr);
         prof_end(p, st);
         p.launches[stage]++;
         return e;

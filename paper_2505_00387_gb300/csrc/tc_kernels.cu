@@ -48,6 +48,7 @@ struct TcArgs {
     int *counter;
     int *err;
     long long total;
+    const long long *__restrict__ qn;     // explicit axis: q_l = q_c + qn[l] eps, else null
     int ntiles, nbins, nq, ntheta, G, Gp, ntr, cq;
     float scale;
 };
@@ -106,6 +107,25 @@ __device__ __forceinline__ void phases8(const TraceGeo &tr, unsigned k, int l0, 
     for (int i = 0; i < 8; ++i) {
         e[i] = l0 + i < nq ? z : make_float2(0.f, 0.f);
         z = cmul2(z, st);
+    }
+}
+
+// The same eight samples on an explicit (non-uniform) curvature axis: the
+// phase of l is k*A + qn[l]*k*B, one rotation per sample.
+__device__ __forceinline__ void phases8_axis(const TraceGeo &tr, unsigned k, int l0,
+                                             const long long *qn, int nq, float sgn, float wgt,
+                                             float2 *e) {
+    const unsigned long long ka = (unsigned long long)k * tr.A;
+    const unsigned long long kb = (unsigned long long)k * tr.B;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int l = l0 + i;
+        if (l < nq) {
+            const float2 z = cis_fixed(ka + (unsigned long long)__ldg(qn + l) * kb, sgn);
+            e[i] = make_float2(z.x * wgt, z.y * wgt);
+        } else {
+            e[i] = make_float2(0.f, 0.f);
+        }
     }
 }
 
@@ -211,7 +231,10 @@ slice_fwd_tc_kernel(const TcArgs a, const float2 *__restrict__ X, float2 *__rest
                 float2 e[8];
                 if (t < t1) {
                     const TraceGeo tr = a.geo[t];
-                    phases8(tr, (unsigned)k, 32 * c + 8 * lb, a.cq, a.nq, -1.f, 1.f, e);
+                    if (a.qn)
+                        phases8_axis(tr, (unsigned)k, 32 * c + 8 * lb, a.qn, a.nq, -1.f, 1.f, e);
+                    else
+                        phases8(tr, (unsigned)k, 32 * c + 8 * lb, a.cq, a.nq, -1.f, 1.f, e);
                 } else {
 #pragma unroll
                     for (int i = 0; i < 8; ++i) e[i] = make_float2(0.f, 0.f);
@@ -362,7 +385,10 @@ slice_adj_tc_kernel(const TcArgs a, const float2 *__restrict__ Yh, float2 *__res
                     unsigned char *ahi = st0 + (2 * mt) * kTileA, *alo = ahi + kTileA;
                     float2 e[8];
                     if (have) {
-                        phases8(tr, (unsigned)k, l0, a.cq, a.nq, 1.f, wgt, e);
+                        if (a.qn)
+                            phases8_axis(tr, (unsigned)k, l0, a.qn, a.nq, 1.f, wgt, e);
+                        else
+                            phases8(tr, (unsigned)k, l0, a.cq, a.nq, 1.f, wgt, e);
                     } else {
 #pragma unroll
                         for (int i = 0; i < 8; ++i) e[i] = make_float2(0.f, 0.f);
@@ -480,6 +506,7 @@ static TcArgs tc_args(const Plan &p, bool adjoint, int *counter) {
     a.Gp = p.tc_gp;
     a.ntr = p.ntr[0];
     a.cq = p.cq;
+    a.qn = p.qexplicit ? p.qn : nullptr;
     a.scale = (float)(1.0 / p.nfft);
     return a;
 }

@@ -33,16 +33,36 @@ def _geom(nt, dt, ntau, nq, q0, dq, ntheta, hx, hy, keep):
 PRECISIONS = {"fp32": L.AAHRT_PRECISION_FP32, "split_bf16": L.AAHRT_PRECISION_SPLIT_BF16}
 
 
-SLICE_INTERPS = {"spread": L.AAHRT_SLICE_SPREAD, "linear_k": L.AAHRT_SLICE_LINEAR_K}
+SLICE_INTERPS = {"spread": L.AAHRT_SLICE_SPREAD, "linear_k": L.AAHRT_SLICE_LINEAR_K,
+                 "direct": L.AAHRT_SLICE_DIRECT}
 
 
 def _opts(interp="keys", spread_width=0, theta_group=0, ngather=1, sigma_t=0.0, fmax=0.0,
           time_pairs=0, autotune=False, precision="fp32", slice_interp="spread",
-          sigma_q=0.0):
+          sigma_q=0.0, q_axis=None, keep=None):
     kind = {"keys": L.AAHRT_INTERP_KEYS, "linear": L.AAHRT_INTERP_LINEAR}[interp]
+    qp = None
+    if q_axis is not None:
+        qa = np.ascontiguousarray(q_axis, dtype=np.float64)
+        if qa.ndim != 1:
+            raise ValueError("q_axis must be 1-D")
+        if keep is not None:
+            keep.append(qa)
+        qp = qa.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     return L.aahrt_opts(kind, int(spread_width), int(theta_group), int(ngather),
                         float(sigma_t), float(fmax), int(time_pairs), int(bool(autotune)),
-                        PRECISIONS[precision], SLICE_INTERPS[slice_interp], float(sigma_q))
+                        PRECISIONS[precision], SLICE_INTERPS[slice_interp], float(sigma_q),
+                        qp)
+
+
+def q_axis_slowness(pmin: float, pmax: float, nq: int) -> np.ndarray:
+    """Uniform-slowness curvature axis q_l = p_l^2 (aahrt_q_axis_slowness)."""
+    return np.array(L.aahrt_q_axis_slowness(pmin, pmax, nq), dtype=np.float64)
+
+
+def nq_required(span: float, fmax: float, r2max: float) -> int:
+    """Curvature samples for a range of width span (eq. q3; aahrt_nq_required)."""
+    return L.aahrt_nq_required(span, fmax, r2max)
 
 
 class AahrtPlan:
@@ -51,7 +71,7 @@ class AahrtPlan:
     def __init__(self, nt, dt, ntau, nq, q0, dq, ntheta, hx, hy, *, interp="keys",
                  spread_width=0, theta_group=0, ngather=1, sigma_t=0.0, fmax=0.0,
                  time_pairs=0, autotune=False, precision="fp32", slice_interp="spread",
-                 sigma_q=0.0, _handle=None, _shapes=None):
+                 sigma_q=0.0, q_axis=None, _handle=None, _shapes=None):
         if _handle is not None:
             self.handle = _handle
         else:
@@ -59,7 +79,8 @@ class AahrtPlan:
             g = _geom(nt, dt, ntau, nq, q0, dq, ntheta, hx, hy, keep)
             self.handle = L.aahrt_plan_create(
                 g, _opts(interp, spread_width, theta_group, ngather, sigma_t, fmax,
-                         time_pairs, autotune, precision, slice_interp, sigma_q))
+                         time_pairs, autotune, precision, slice_interp, sigma_q, q_axis,
+                         keep))
         self.info = L.aahrt_plan_query(self.handle)
         self.nt, self.ntau, self.nq, self.ntheta = nt, ntau, nq, ntheta
         self.device = torch.device("cuda", torch.cuda.current_device())
@@ -71,13 +92,13 @@ class AahrtPlan:
     @classmethod
     def batched(cls, gathers: Sequence, interp="keys", spread_width=0, theta_group=0,
                 sigma_t=0.0, fmax=0.0, time_pairs=0, autotune=False, slice_interp="spread",
-                sigma_q=0.0):
+                sigma_q=0.0, q_axis=None):
         keep = []
         geoms = [_geom(g.nt, g.dt, g.ntau, g.nq, g.q0, g.dq, g.ntheta, g.hx, g.hy, keep)
                  for g in gathers]
         h = L.aahrt_plan_create_batched(
             geoms, _opts(interp, spread_width, theta_group, 1, sigma_t, fmax, time_pairs,
-                         autotune, "fp32", slice_interp, sigma_q))
+                         autotune, "fp32", slice_interp, sigma_q, q_axis, keep))
         g0 = gathers[0]
         return cls(g0.nt, g0.dt, g0.ntau, g0.nq, g0.q0, g0.dq, g0.ntheta, None, None,
                    _handle=h)
@@ -116,6 +137,18 @@ class AahrtPlan:
         self._check(m, self.model_len, "m")
         L.aahrt_adjoint(self.handle, d.data_ptr(), m.data_ptr(), _stream_ptr(stream))
         return m
+
+    def partial_nmo(self, d: torch.Tensor, q_ref: float, out: Optional[torch.Tensor] = None,
+                    transpose: bool = False, stream=None):
+        """Partial NMO of the data by q_ref (Sec. 3.5): curvature q -> q - q_ref
+        (or the map's exact transpose)."""
+        self._check(d, self.data_len, "d")
+        if out is None:
+            out = torch.empty(self.data_len, device=d.device, dtype=torch.float32)
+        self._check(out, self.data_len, "out")
+        L.aahrt_partial_nmo(self.handle, d.data_ptr(), out.data_ptr(), float(q_ref),
+                            transpose, _stream_ptr(stream))
+        return out
 
     def sparse_solve(self, d: torch.Tensor, lam: float, iters: int,
                      m: Optional[torch.Tensor] = None, *, ista=False, gamma=0.0,

@@ -1,0 +1,288 @@
+"""GPU: explicit (uniform-slowness) curvature axes, the direct-sum slice step
+and the partial NMO (Sec. 3.5) through the C ABI, against the oracle on the
+same seeded inputs.
+
+* the direct sum on the uniform axis and on uniform-slowness and centred
+  (negative) axes: forward / adjoint <= 1e-4, FP32 dot test <= 1e-6, FISTA
+  <= 1e-3; groups of several slices, a ragged q count and an adjoint whose
+  traces do not fit one staging pass;
+* the tensor-core contraction on a uniform-slowness axis (3 gathers) and a
+  batched plan of cubes with it;
+* the q-moment pick on the explicit axis;
+* partial NMO: forward and transpose (Keys and linear) against the oracle,
+  muted zones, the gathers-fastest and batched layouts, and the pipeline
+  partial NMO -> solve on the centred axis of eq. q3;
+* paper-scale gather (2000 traces, 100 uniform-slowness curvatures): sampled
+  traces and slices of the forward and adjoint.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import fista, ops, pick, pnmo
+from paper_2505_00387_gb300 import synthetic as syn
+
+from gpu_util import dev, gpu_plan, host, oracle_plan, rel
+
+pytestmark = pytest.mark.gpu
+
+TOL_OP = 1e-4
+TOL_FISTA = 1e-3
+TOL_DOT = 1e-6
+
+
+def slowness_axis(nq):
+    return pnmo.q_axis_slowness(syn.P_MIN, syn.P_MAX, nq)
+
+
+def dot_rel(gp, shape_m, shape_d, seed):
+    rng = np.random.default_rng(seed)
+    m = rng.standard_normal(shape_m).astype(np.float32).astype(np.float64)
+    d = rng.standard_normal(shape_d).astype(np.float32).astype(np.float64)
+    lhs = float(np.sum(host(gp.forward(dev(m))) * d.ravel()))
+    rhs = float(np.sum(host(gp.adjoint(dev(d))) * m.ravel()))
+    return abs(lhs - rhs) / abs(lhs)
+
+
+CASES = {
+    "uniform_direct": dict(q=None, slice_interp="direct"),
+    "slowness": dict(q="slowness"),
+    "centred": dict(q="centred"),
+    "slowness_groups": dict(q="slowness", theta_group=3),
+}
+
+
+def make_case(name, nq=32):
+    g = syn.config0()
+    c = CASES[name]
+    qa = None
+    if c["q"] == "slowness":
+        qa = slowness_axis(nq)
+    elif c["q"] == "centred":
+        qa = np.linspace(-1.4e-7, 1.1e-7, nq)
+    kw = {}
+    if "theta_group" in c:
+        kw["theta_group"] = c["theta_group"]
+    op = oracle_plan(g, q_axis=qa)
+    gp = gpu_plan(g, q_axis=qa, slice_interp=c.get("slice_interp", "spread"), **kw)
+    return g, op, gp
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_direct_forward_adjoint_dot(name):
+    g, op, gp = make_case(name)
+    assert gp.info.slice_interp == 2
+    rng = np.random.default_rng(120)
+    m = rng.standard_normal((g.ntau, g.nq, g.ntheta))
+    d = rng.standard_normal((g.nt, g.ntr))
+    assert rel(host(gp.forward(dev(m)), d.shape), ops.forward(op, m)) < TOL_OP
+    assert rel(host(gp.adjoint(dev(d)), m.shape), ops.adjoint(op, d)) < TOL_OP
+    assert dot_rel(gp, m.shape, d.shape, 121) < TOL_DOT
+
+
+@pytest.mark.parametrize("name", ["slowness", "centred"])
+def test_direct_fista(name):
+    g, op, gp = make_case(name)
+    m_true = np.zeros((g.ntau, g.nq, g.ntheta))
+    rng = np.random.default_rng(122)
+    for _ in range(5):
+        m_true[rng.integers(20, g.ntau - 20), rng.integers(0, g.nq), rng.integers(0, g.ntheta)] = 1.0
+    d = ops.forward(op, m_true)
+    gamma = float(np.float32(0.95 / fista.power_sigma2(op, d)))
+    lam = float(np.float32(0.05 * np.abs(ops.adjoint(op, d)).max()))
+    ref = fista.solve(op, d, lam, 20, gamma)
+    for graph in (True, False):
+        mg, _ = gp.sparse_solve(dev(d), lam, 20, gamma=gamma, use_graph=graph, want_info=False)
+        assert rel(host(mg, ref.shape), ref) < TOL_FISTA
+
+
+def test_direct_ragged_and_chunked_adjoint():
+    """4000 traces in one azimuth group: the adjoint stages them in two
+    passes; 19 curvatures leave a ragged last warp of lanes."""
+    rng = np.random.default_rng(123)
+    nt, dt, nq, nth = 64, 0.008, 19, 4
+    hx, hy = syn.disc_offsets(rng, 4000, 1500.0)
+    qa = slowness_axis(nq)
+    op = oracle.make_plan(nt, dt, nt, nq, 0.0, 0.0, nth, hx, hy, q_axis=qa)
+    from paper_2505_00387_gb300.plan import AahrtPlan
+    gp = AahrtPlan(nt, dt, nt, nq, 0.0, 0.0, nth, hx, hy, q_axis=qa)
+    m = rng.standard_normal((nt, nq, nth))
+    d = rng.standard_normal((nt, 4000))
+    assert rel(host(gp.forward(dev(m)), d.shape), ops.forward(op, m)) < TOL_OP
+    assert rel(host(gp.adjoint(dev(d)), m.shape), ops.adjoint(op, d)) < TOL_OP
+    assert dot_rel(gp, m.shape, d.shape, 124) < TOL_DOT
+
+
+def test_tensorcore_on_slowness_axis():
+    g = syn.config0()
+    qa = slowness_axis(g.nq)
+    op = oracle_plan(g, q_axis=qa)
+    G = 3
+    gp = gpu_plan(g, ngather=G, precision="split_bf16", q_axis=qa)
+    rng = np.random.default_rng(125)
+    ms = [rng.standard_normal((g.ntau, g.nq, g.ntheta)) for _ in range(G)]
+    ds = [rng.standard_normal((g.nt, g.ntr)) for _ in range(G)]
+    dg = host(gp.forward(dev(np.stack(ms, axis=-1)))).reshape(g.nt, g.ntr, G)
+    mg = host(gp.adjoint(dev(np.stack(ds, axis=-1)))).reshape(g.ntau, g.nq, g.ntheta, G)
+    gp.status()
+    for i in range(G):
+        assert rel(dg[..., i], ops.forward(op, ms[i])) < TOL_OP
+        assert rel(mg[..., i], ops.adjoint(op, ds[i])) < TOL_OP
+
+
+def test_batched_cubes_on_slowness_axis():
+    from paper_2505_00387_gb300.plan import AahrtPlan
+    cubes = syn.config3(cubes=[1, 5, 9])
+    for c in cubes:                       # a shorter time axis keeps the oracle quick
+        c.nt = c.ntau = 300
+    qa = slowness_axis(cubes[0].nq)
+    gp = AahrtPlan.batched(cubes, q_axis=qa)
+    r2max = max(float(np.max(c.hx ** 2 + c.hy ** 2)) for c in cubes)
+    rng = np.random.default_rng(126)
+    ms = [rng.standard_normal((c.ntau, c.nq, c.ntheta)) for c in cubes]
+    dg = host(gp.forward(dev(np.concatenate([m.ravel() for m in ms]))))
+    off = 0
+    for c, m in zip(cubes, ms):
+        op = oracle.make_plan(**c.geom_kwargs(), r2max=r2max, q_axis=qa)
+        n = c.nt * c.hx.size
+        assert rel(dg[off:off + n].reshape(c.nt, -1), ops.forward(op, m)) < TOL_OP
+        off += n
+
+
+def test_pick_on_slowness_axis():
+    g, op, gp = make_case("slowness")
+    rng = np.random.default_rng(127)
+    m = rng.standard_normal((g.ntau, g.nq, g.ntheta))
+    qh, w = gp.pick_velocity(dev(m))
+    q_ref, w_ref = pick.pick(op, m.astype(np.float32).astype(np.float64))
+    assert rel(host(qh, q_ref.shape), q_ref) < 1e-6
+    assert rel(host(w, w_ref.shape), w_ref) < 1e-6
+
+
+def test_explicit_axis_refusals():
+    from paper_2505_00387_gb300._lib import AahrtError
+    g = syn.config0()
+    qa = slowness_axis(g.nq)
+    with pytest.raises(AahrtError):
+        gpu_plan(g, q_axis=qa, slice_interp="linear_k")
+    bad = qa.copy()
+    bad[3] = np.nan
+    with pytest.raises(AahrtError):
+        gpu_plan(g, q_axis=bad)
+    gp = gpu_plan(g, q_axis=qa)
+    with pytest.raises(AahrtError):
+        gp.velocity_scan_grid(dev(np.zeros((g.nt, g.ntr))),
+                              (16, 16, -1000.0, 2000.0 / 15, -1000.0, 2000.0 / 15))
+
+
+# ------------------------------------------------------------- partial NMO
+def pnmo_case(interp, ntr=300, nt=500):
+    rng = np.random.default_rng(128)
+    hx, hy = syn.disc_offsets(rng, ntr, 2500.0)
+    q0, dq = syn.q_axis(8)
+    op = oracle.make_plan(nt, 0.004, nt, 8, q0, dq, 6, hx, hy, interp=interp)
+    from paper_2505_00387_gb300.plan import AahrtPlan
+    gp = AahrtPlan(nt, 0.004, nt, 8, q0, dq, 6, hx, hy, interp=interp)
+    return op, gp, rng
+
+
+@pytest.mark.parametrize("interp", ["keys", "linear"])
+@pytest.mark.parametrize("q_ref", [2.3e-7, -1.7e-7, 0.0])
+def test_partial_nmo_matches_oracle(interp, q_ref):
+    op, gp, rng = pnmo_case(interp)
+    d = rng.standard_normal((op.nt, op.ntr)).astype(np.float32).astype(np.float64)
+    e = rng.standard_normal((op.nt, op.ntr)).astype(np.float32).astype(np.float64)
+    out = host(gp.partial_nmo(dev(d), q_ref), d.shape)
+    want = pnmo.partial_nmo(op, d, q_ref)
+    assert rel(out, want) < 1e-6
+    np.testing.assert_array_equal(out == 0.0, want == 0.0)      # same muted samples
+    outT = host(gp.partial_nmo(dev(e), q_ref, transpose=True), d.shape)
+    assert rel(outT, pnmo.partial_nmo_T(op, e, q_ref)) < 1e-6
+    lhs, rhs = float(np.sum(out * e)), float(np.sum(d * outT))
+    assert abs(lhs - rhs) <= 1e-6 * abs(lhs)
+
+
+def test_partial_nmo_layouts():
+    """Gathers stored fastest (tensor-core plan) and batched cubes."""
+    from paper_2505_00387_gb300.plan import AahrtPlan
+    g = syn.config0()
+    op = oracle_plan(g)
+    G = 3
+    gp = gpu_plan(g, ngather=G, precision="split_bf16")
+    rng = np.random.default_rng(129)
+    ds = [rng.standard_normal((g.nt, g.ntr)) for _ in range(G)]
+    out = host(gp.partial_nmo(dev(np.stack(ds, axis=-1)), 1.5e-7)).reshape(g.nt, g.ntr, G)
+    for i in range(G):
+        want = pnmo.partial_nmo(op, ds[i].astype(np.float32).astype(np.float64), 1.5e-7)
+        assert rel(out[..., i], want) < 1e-6
+    cubes = syn.config3(cubes=[2, 3])
+    gb = AahrtPlan.batched(cubes)
+    dd = [c.d.astype(np.float32).astype(np.float64) for c in cubes]
+    out = host(gb.partial_nmo(dev(np.concatenate([x.ravel() for x in dd])), -9e-8))
+    off = 0
+    for c, x in zip(cubes, dd):
+        opc = oracle.make_plan(**c.geom_kwargs())
+        n = x.size
+        assert rel(out[off:off + n].reshape(x.shape), pnmo.partial_nmo(opc, x, -9e-8)) < 1e-6
+        off += n
+
+
+def test_partial_nmo_rejects_bad_arguments():
+    from paper_2505_00387_gb300._lib import AahrtError
+    op, gp, rng = pnmo_case("keys")
+    d = dev(np.zeros((op.nt, op.ntr)))
+    with pytest.raises(AahrtError):
+        gp.partial_nmo(d, float("nan"))
+    with pytest.raises(AahrtError):
+        gp.partial_nmo(d, 1e-7, out=d)
+
+
+def test_partial_nmo_then_centred_solve():
+    """Events in [q_a, q_b]: partial NMO by the range centre, then FISTA on
+    the centred axis of eq. q3's sample count, GPU against the oracle's same
+    pipeline."""
+    from oracle import checks
+    nt, dt, nth = 200, 0.008, 2
+    hx, hy = syn.grid_offsets(8, 1400.0)
+    qa, qb = (1 / 3000.0) ** 2, (1 / 2000.0) ** 2
+    q_ref = 0.5 * (qa + qb)
+    fmax = 12.0
+    r2max = float(np.max(hx * hx + hy * hy))
+    from paper_2505_00387_gb300.plan import AahrtPlan, nq_required
+    nq = nq_required(qb - qa, fmax, r2max) + 2
+    assert nq == pnmo.nq_required(qb - qa, fmax, r2max) + 2
+    half = 0.5 * (qb - qa) * nq / (nq - 2)
+    qc = np.linspace(-half, half, nq)
+    op = oracle.make_plan(nt, dt, nt, nq, 0.0, 0.0, nth, hx, hy, q_axis=qc, fmax=fmax)
+    gp = AahrtPlan(nt, dt, nt, nq, 0.0, 0.0, nth, hx, hy, q_axis=qc, fmax=fmax)
+    w = [{int(op.j0[h]): op.w0[h]} for h in range(op.ntr)]
+    for h in range(op.ntr):
+        w[h][int(op.j1[h])] = w[h].get(int(op.j1[h]), 0.0) + op.w1[h]
+    ev = [(1.0, 0.35, 6.0, qa + 0.2 * (qb - qa), 0), (1.0, 0.75, 6.0, qa + 0.8 * (qb - qa), 0)]
+    d = checks.riemann_sum_forward(nt, dt, op.r2, w, ev).astype(np.float32).astype(np.float64)
+    dn_ref = pnmo.partial_nmo(op, d, q_ref)
+    dn = gp.partial_nmo(dev(d), q_ref)
+    assert rel(host(dn, dn_ref.shape), dn_ref) < 1e-6
+    gamma = float(np.float32(0.95 / fista.power_sigma2(op, dn_ref, iters=30)))
+    lam = float(np.float32(0.05 * np.abs(ops.adjoint(op, dn_ref)).max()))
+    ref = fista.solve(op, dn_ref, lam, 40, gamma)
+    mg, _ = gp.sparse_solve(dn, lam, 40, gamma=gamma, want_info=False)
+    assert rel(host(mg, ref.shape), ref) < TOL_FISTA
+
+
+# ------------------------------------------------- paper-scale gather
+def test_config1_slowness_axis_sampled():
+    g = syn.config1()
+    qa = slowness_axis(g.nq)
+    op = oracle_plan(g, q_axis=qa)
+    gp = gpu_plan(g, q_axis=qa)
+    rng = np.random.default_rng(130)
+    m = rng.standard_normal((g.ntau, g.nq, g.ntheta)).astype(np.float32).astype(np.float64)
+    dg = host(gp.forward(dev(m)), (g.nt, g.ntr))
+    traces = [0, 11, 1000, 1999]
+    assert rel(dg[:, traces], ops.forward_traces(op, m, traces)) < TOL_OP
+    mg = host(gp.adjoint(dev(g.d)), (g.ntau, g.nq, g.ntheta))
+    slices = [0, 20, g.ntheta - 1]
+    assert rel(mg[:, :, slices], ops.adjoint_slices(op, g.d, slices)) < TOL_OP
+    assert dot_rel(gp, m.shape, (g.nt, g.ntr), 131) < TOL_DOT

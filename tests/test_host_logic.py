@@ -66,3 +66,21 @@ def test_trace_taps_exact(tmp_path):
         want = np.exp(beta * (np.sqrt(np.clip(1 - t * t, 0, None)) - 1))
         # polynomial fit + float rounding; the edge discontinuity e^-beta bounds it
         np.testing.assert_allclose(phi, want, rtol=0, atol=2e-6 + 4 * np.exp(-beta))
+
+
+def test_curvature_axis_helpers_match_oracle():
+    """aahrt_q_axis_slowness and aahrt_nq_required (host functions of the
+    library, no device work) against the oracle's uniform-slowness axis and
+    eq. q3 count."""
+    from oracle import pnmo
+    from paper_2505_00387_gb300 import _lib as L
+    for pmin, pmax, nq in ((1 / 3500.0, 1 / 1500.0, 100), (1 / 3000.0, 1 / 2000.0, 1),
+                           (2e-4, 6e-4, 7)):
+        q = np.array(L.aahrt_q_axis_slowness(pmin, pmax, nq))
+        np.testing.assert_allclose(q, pnmo.q_axis_slowness(pmin, pmax, nq), rtol=1e-15)
+    for span, fmax, r2max in ((6.2e-7, 60.0, 4.5e6), (0.0, 10.0, 1e6), (1.98e-7, 12.0, 3.9e6)):
+        assert L.aahrt_nq_required(span, fmax, r2max) == pnmo.nq_required(span, fmax, r2max)
+    with pytest.raises(L.AahrtError):
+        L.aahrt_nq_required(-1.0, 1.0, 1.0)
+    with pytest.raises(L.AahrtError):
+        L.aahrt_q_axis_slowness(1e-4, float("nan"), 4)
