@@ -38,6 +38,8 @@ __device__ __forceinline__ RowRange load_rng(const RowRange *p) {
     return RowRange{v.x, v.y};
 }
 
+constexpr int kPackBatch = 8;   // spectrum loads in flight per thread (c2r pack)
+
 template <int P>
 struct Acc {
     float2 v[P];
@@ -139,12 +141,22 @@ r2c_kernel(const float *__restrict__ in, float2 *__restrict__ out,
     float *stg = reinterpret_cast<float *>(sm + P * ld);          // staged input [row][2P]
     float *sfr = stg + nrow_in * 2 * P;                           // source fractions (TRANS)
 
-    // stage the block's input columns (independent, coalesced loads)
+    // stage the block's input columns (independent, coalesced loads, a batch
+    // of rounds in flight per thread)
     const float *src = in + cg.real_off;
-    for (int idx = threadIdx.x; idx < nrow_in * 2 * P; idx += blockDim.x) {
-        const int r = idx >> (LP + 1);
-        const int c = idx & (2 * P - 1);
-        stg[idx] = c < cg.ncol ? __ldg(src + (long long)r * cg.ld_real + c) : 0.f;
+    const int total = nrow_in * 2 * P;
+    for (int base = threadIdx.x; base < total; base += kPackBatch * blockDim.x) {
+        float v[kPackBatch];
+#pragma unroll
+        for (int u = 0; u < kPackBatch; ++u) {
+            const int idx = base + u * blockDim.x;
+            const int r = idx >> (LP + 1);
+            const int c = idx & (2 * P - 1);
+            v[u] = (idx < total && c < cg.ncol) ? __ldg(src + (long long)r * cg.ld_real + c) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < kPackBatch; ++u)
+            if (base + u * blockDim.x < total) stg[base + u * blockDim.x] = v[u];
     }
     if (TRANS)
         for (int idx = threadIdx.x; idx < rs.npos; idx += blockDim.x)
@@ -174,29 +186,44 @@ __device__ __forceinline__ void c2r_core(float2 *sm, float *sfr, const float2 *_
     if (TRANS)
         for (int idx = threadIdx.x; idx < rs.npos; idx += blockDim.x)
             sfr[idx] = __ldg(&rs.pos[idx].fr);
-    // pack Z = A + iB over the full frame, bit-reversed for the DIT pass
-    for (int idx = threadIdx.x; idx < P * (half + 1); idx += blockDim.x) {
-        const int p = idx & (P - 1);
-        const int k = idx >> LP;
-        float2 zk = make_float2(0.f, 0.f), zn = zk;
-        if (k < nbins && p < npair) {
-            const long long o = (long long)k * cg.ld_spec + 2 * p;
-            // the fused kernel rewrites the spectrum later: plain loads there
-            float2 A = STAGE ? src[o] : __ldg(src + o);
-            float2 B = (2 * p + 1 < cg.ncol) ? (STAGE ? src[o + 1] : __ldg(src + o + 1))
-                                             : make_float2(0.f, 0.f);
-            if (k == 0) { A.y = 0.f; B.y = 0.f; }
-            zk = make_float2(A.x - B.y, A.y + B.x);   // A + iB
-            zn = make_float2(A.x + B.y, B.x - A.y);   // conj(A) + i conj(B)
+    // pack Z = A + iB over the full frame, bit-reversed for the DIT pass;
+    // kPackBatch rounds of loads are issued before any is used, so each
+    // thread keeps that many spectrum reads in flight
+    const int total = P * (half + 1);
+    for (int base = threadIdx.x; base < total; base += kPackBatch * blockDim.x) {
+        float2 A[kPackBatch], B[kPackBatch];
+#pragma unroll
+        for (int u = 0; u < kPackBatch; ++u) {
+            const int idx = base + u * blockDim.x;
+            const int p = idx & (P - 1);
+            const int k = idx >> LP;
+            A[u] = B[u] = make_float2(0.f, 0.f);
+            if (idx < total && k < nbins && p < npair) {
+                const long long o = (long long)k * cg.ld_spec + 2 * p;
+                // the fused kernel rewrites the spectrum later: plain loads there
+                A[u] = STAGE ? src[o] : __ldg(src + o);
+                if (2 * p + 1 < cg.ncol) B[u] = STAGE ? src[o + 1] : __ldg(src + o + 1);
+            }
         }
-        float2 *q = sm + p * ld;
-        if (k == 0) {
-            q[padi(0)] = zk;
-        } else if (k == half) {
-            q[padi(brev_bits(half, L))] = make_float2(0.f, 0.f);
-        } else {
-            q[padi(brev_bits(k, L))] = zk;
-            q[padi(brev_bits(N - k, L))] = zn;
+#pragma unroll
+        for (int u = 0; u < kPackBatch; ++u) {
+            const int idx = base + u * blockDim.x;
+            if (idx >= total) break;
+            const int p = idx & (P - 1);
+            const int k = idx >> LP;
+            float2 a = A[u], b = B[u];
+            if (k == 0) { a.y = 0.f; b.y = 0.f; }
+            const float2 zk = make_float2(a.x - b.y, a.y + b.x);   // A + iB
+            const float2 zn = make_float2(a.x + b.y, b.x - a.y);   // conj(A) + i conj(B)
+            float2 *q = sm + p * ld;
+            if (k == 0) {
+                q[padi(0)] = zk;
+            } else if (k == half) {
+                q[padi(brev_bits(half, L))] = make_float2(0.f, 0.f);
+            } else {
+                q[padi(brev_bits(k, L))] = zk;
+                q[padi(brev_bits(N - k, L))] = zn;
+            }
         }
     }
     __syncthreads();
