@@ -168,22 +168,25 @@ def launch_bytes(info, launches, iters_total):
     return sb
 
 
-def traffic_record(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources."""
+def traffic_record(stage):
+    """DRAM bytes per launch of a stage's kernel from the committed ncu
+    summary, if the files that define that kernel (its source, the headers it
+    includes and the plan code that sizes its launch) still hash to the ones
+    the counters were taken on."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     try:
-        rec = json.load(open(path))
-        h = hashlib.sha256()
-        csrc = os.path.join(ROOT, "paper_2505_00387_gb300", "csrc")
-        for f in sorted(os.listdir(csrc)):
-            h.update(open(os.path.join(csrc, f), "rb").read())
-        if rec.get("csrc_sha256") != h.hexdigest():
+        rec = json.load(open(path)).get("kernels", {}).get(stage)
+        if rec is None:
             return None
-        return rec.get("kernels", {}).get(kernel)
+        h = hashlib.sha256()
+        for f in rec["files"]:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        if rec.get("sha256") != h.hexdigest():
+            return None
+        return rec.get("dram_bytes")
     except Exception:
         return None
 

@@ -9,22 +9,26 @@
 // The phase in cycles is f_k q_l r_h^2 = k A_h + n_l k B_h with the axis
 // written as q_l = q_c + n_l eps (integer n_l), A_h = q_c r_h^2/(Nfft ds) and
 // B_h = eps r_h^2/(Nfft ds) in 0.64 fixed point: the products wrap modulo
-// 2^64, so the fraction of a cycle is exact up to the rounding of A_h and B_h.
+// 2^64, so the fraction of a cycle is exact up to the rounding of A_h and B_h;
+// per term only its top 32 bits are formed, from two 32-bit multiply-adds.
 //
 // Work items are (cube, azimuth group, bin) as in the spreading kernels.
 // Forward: the item's slice columns of X[k] are staged in shared memory and
-// each thread sums one trace over l.  Adjoint: the item's traces (y, weights,
-// k A_h, k B_h) are staged in chunks; each warp owns
-// 32 curvatures of the traces of one first slice, evaluates every phase once
-// and sums it with weight w0 (for that slice) and w1 (for the next) into two
-// accumulator planes, every lane reading the same trace (shared-memory
-// broadcast); each accumulator has one writer, so the order of the sums is
-// fixed (no atomics).
+// each thread sums one trace over l (in four interleaved partial sums).
+// Adjoint: the item's traces (y, weights, phase constants) are staged in
+// chunks; each lane owns one (first slice, curvature) pair -- consecutive
+// lanes take consecutive pairs, so a warp reads one or two traces at a time
+// (shared-memory broadcast) -- evaluates every phase once and sums it with
+// weight w0 (for that slice) and w1 (for the next) into two accumulator
+// planes; each accumulator has one writer, so the order of the sums is fixed
+// (no atomics).
 #include <algorithm>
 
 #include "internal.cuh"
 
 namespace aahrt {
+
+constexpr int kDirectLanes = 4;   // interleaved partial sums per output (fixed below)
 
 struct DirectArgs {
     const TraceGeo *__restrict__ geo;
@@ -37,21 +41,41 @@ struct DirectArgs {
     float scale;
 };
 
-// (cos, sin) of 2 pi x for a fixed-point fraction x of a cycle (2^-64 units)
-__device__ __forceinline__ void cis64(unsigned long long x, float *c, float *s) {
-    const float f = (float)(int)(unsigned)(x >> 32) * 2.3283064365386963e-10f;   // [-1/2, 1/2)
-    __sincosf(6.28318530717958647692f * f, s, c);
+// The top 32 bits of the phase k A + n_l k B (mod 2^64) from 32-bit
+// multiplies: with n' = n_l + 2^31 (0 <= n' < 2^32 since |n_l| <= 2^30) and
+// A' = k A - 2^31 k B, the sum is A' + n' k B, whose top word is
+//   hi(A') + lo(n' hi(kB)) + hi(n' lo(kB))
+// up to the carry of the low words (at most 2^-32 cycle, dropped).  The
+// forward and the adjoint evaluate it through the same code, so their phases
+// agree bit for bit.
+struct Phase32 {
+    unsigned hiA, bh, bl, pad;
+};
+
+__device__ __forceinline__ Phase32 phase_consts(unsigned long long kA, unsigned long long kB) {
+    const unsigned long long ap = kA - (kB << 31);
+    return Phase32{(unsigned)(ap >> 32), (unsigned)(kB >> 32), (unsigned)kB, 0u};
+}
+
+__device__ __forceinline__ unsigned phase_top(unsigned np, const Phase32 &p) {
+    return __umulhi(np, p.bl) + (np * p.bh + p.hiA);
+}
+
+// (cos, sin) of 2 pi t 2^-32 for a signed fraction t of a cycle
+__device__ __forceinline__ void cis32(unsigned t, float *c, float *s) {
+    __sincosf((float)(int)t * 1.4629180792671596e-9f, s, c);   // 2 pi / 2^32
 }
 
 size_t direct_smem_fwd(int tgroup, int extra, int nq) {
-    return (size_t)(tgroup + extra) * nq * sizeof(float2) + (size_t)nq * sizeof(long long);
+    return (size_t)(tgroup + extra) * nq * sizeof(float2) + (size_t)(nq + 1) / 2 * 8;
 }
 
-// chunk staged traces of 32 bytes ((y re, y im, w0, w1) and (k A, k B)),
-// two accumulator planes nq x tgroup (w0 and w1 parts), then the n_l table
+// chunk staged traces of 32 bytes ((y re, y im, w0, w1) and the phase
+// constants), two accumulator planes nq x tgroup (w0 and w1 parts), then the
+// n' table
 size_t direct_smem_adj(int tgroup, int nq, int chunk) {
-    return 2 * (size_t)tgroup * nq * sizeof(float2) + (size_t)nq * sizeof(long long) +
-           (size_t)chunk * (sizeof(float4) + sizeof(ulonglong2));
+    return 2 * (size_t)tgroup * nq * sizeof(float2) + (size_t)nq * sizeof(unsigned) +
+           (size_t)chunk * (sizeof(float4) + sizeof(Phase32));
 }
 
 __global__ void __launch_bounds__(kThreadsSlice, 3)
@@ -59,9 +83,10 @@ direct_fwd_kernel(const DirectArgs a, const float2 *__restrict__ X, float2 *__re
     extern __shared__ float4 smem_f4[];
     __shared__ long long s_item;
     const int extra = a.ngroup > 1 ? 1 : 0;
-    long long *s_qn = reinterpret_cast<long long *>(smem_f4);
-    float2 *Xs = reinterpret_cast<float2 *>(s_qn + a.nq);       // [l][nj + extra]
-    for (int l = threadIdx.x; l < a.nq; l += blockDim.x) s_qn[l] = a.qn[l];
+    float2 *Xs = reinterpret_cast<float2 *>(smem_f4);          // [jj][l]
+    unsigned *s_np = reinterpret_cast<unsigned *>(Xs + (size_t)(a.tgroup + extra) * a.nq);
+    for (int l = threadIdx.x; l < a.nq; l += blockDim.x)
+        s_np[l] = (unsigned)((unsigned long long)a.qn[l] + 0x80000000ull);
     for (;;) {
         if (threadIdx.x == 0) s_item = (long long)atomicAdd(a.counter, 1);
         __syncthreads();
@@ -71,14 +96,15 @@ direct_fwd_kernel(const DirectArgs a, const float2 *__restrict__ X, float2 *__re
         const int k = (int)(item - (long long)gi * a.nbins);
         const SliceGroup g = a.groups[gi];
         const int ncol = g.nj + extra;
-        // stage X[k][l][ja + jj] (slice index mod ntheta) as Xs[l][jj]
+        // stage X[k][l][ja + jj] (slice index mod ntheta) as Xs[jj][l], so a
+        // trace walks its slices' curvatures at unit stride
         const float2 *Xk = X + g.x_off + (long long)k * a.nq * a.ntheta;
         for (int idx = threadIdx.x; idx < a.nq * ncol; idx += blockDim.x) {
             const int l = idx / ncol;
             const int jj = idx - l * ncol;
             int j = g.ja + jj;
             if (j >= a.ntheta) j -= a.ntheta;
-            Xs[idx] = __ldg(Xk + (long long)l * a.ntheta + j);
+            Xs[jj * a.nq + l] = __ldg(Xk + (long long)l * a.ntheta + j);
         }
         __syncthreads();
 
@@ -94,23 +120,34 @@ direct_fwd_kernel(const DirectArgs a, const float2 *__restrict__ X, float2 *__re
                 jj1 = tr.j0 + 1;
                 if (jj1 == a.ntheta) jj1 = 0;
             }
-            const unsigned long long kA = (unsigned long long)k * tr.A;
-            const unsigned long long kB = (unsigned long long)k * tr.B;
-            const float2 *X0 = Xs + jj0;
-            const float2 *X1 = Xs + jj1;
-            float ar = 0.f, ai = 0.f;
-#pragma unroll 4
-            for (int l = 0; l < a.nq; ++l) {
-                float c, s;
-                cis64(kA + (unsigned long long)s_qn[l] * kB, &c, &s);
-                const float2 x0 = X0[l * ncol], x1 = X1[l * ncol];
-                const float vr = fmaf(tr.w0, x0.x, tr.w1 * x1.x);
-                const float vi = fmaf(tr.w0, x0.y, tr.w1 * x1.y);
-                // v * exp(-2 pi i ph) = v (c - i s)
-                ar = fmaf(vr, c, fmaf(vi, s, ar));
-                ai = fmaf(vi, c, fmaf(-vr, s, ai));
+            const Phase32 ph = phase_consts((unsigned long long)k * tr.A,
+                                            (unsigned long long)k * tr.B);
+            const float2 *X0 = Xs + jj0 * a.nq;
+            const float2 *X1 = Xs + jj1 * a.nq;
+            // curvature l goes to partial sum l mod kDirectLanes; the partial
+            // sums (fewer terms each: smaller rounding of the random-phase
+            // sum) are added in a fixed order at the end
+            float ar[kDirectLanes], ai[kDirectLanes];
+#pragma unroll
+            for (int u = 0; u < kDirectLanes; ++u) ar[u] = ai[u] = 0.f;
+            for (int l = 0; l < a.nq; l += kDirectLanes) {
+#pragma unroll
+                for (int u = 0; u < kDirectLanes; ++u) {
+                    if (l + u < a.nq) {
+                        float c, s;
+                        cis32(phase_top(s_np[l + u], ph), &c, &s);
+                        const float2 x0 = X0[l + u], x1 = X1[l + u];
+                        const float vr = fmaf(tr.w0, x0.x, tr.w1 * x1.x);
+                        const float vi = fmaf(tr.w0, x0.y, tr.w1 * x1.y);
+                        // v * exp(-2 pi i ph) = v (c - i s)
+                        ar[u] = fmaf(vr, c, fmaf(vi, s, ar[u]));
+                        ai[u] = fmaf(vi, c, fmaf(-vr, s, ai[u]));
+                    }
+                }
             }
-            Yk[tr.col] = make_float2(a.scale * ar, a.scale * ai);
+            const float sr = (ar[0] + ar[1]) + (ar[2] + ar[3]);
+            const float si = (ai[0] + ai[1]) + (ai[2] + ai[3]);
+            Yk[tr.col] = make_float2(a.scale * sr, a.scale * si);
         }
         __syncthreads();
     }
@@ -121,13 +158,13 @@ direct_adj_kernel(const DirectArgs a, const float2 *__restrict__ Y, float2 *__re
     extern __shared__ float4 smem_f4[];
     __shared__ long long s_item;
     float4 *s_y = smem_f4;                                                  // [chunk]
-    ulonglong2 *s_ph = reinterpret_cast<ulonglong2 *>(s_y + a.chunk);      // (k A, k B)
+    Phase32 *s_ph = reinterpret_cast<Phase32 *>(s_y + a.chunk);            // phase constants
     float2 *acc0 = reinterpret_cast<float2 *>(s_ph + a.chunk);             // [l][nj], w0 parts
     float2 *acc1 = acc0 + (size_t)a.tgroup * a.nq;                          // [l][nj], w1 parts
-    long long *s_qn = reinterpret_cast<long long *>(acc1 + (size_t)a.tgroup * a.nq);
-    for (int l = threadIdx.x; l < a.nq; l += blockDim.x) s_qn[l] = a.qn[l];
+    unsigned *s_np = reinterpret_cast<unsigned *>(acc1 + (size_t)a.tgroup * a.nq);
+    for (int l = threadIdx.x; l < a.nq; l += blockDim.x)
+        s_np[l] = (unsigned)((unsigned long long)a.qn[l] + 0x80000000ull);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nlb = (a.nq + 31) >> 5;
     const bool several = a.ngroup > 1;
     for (;;) {
         if (threadIdx.x == 0) s_item = (long long)atomicAdd(a.counter, 1);
@@ -159,14 +196,18 @@ direct_adj_kernel(const DirectArgs a, const float2 *__restrict__ Y, float2 *__re
                 const TraceGeo tr = geo[t];
                 const float2 y = __ldg(Yk + tr.col);
                 s_y[i] = make_float4(a.scale * y.x, a.scale * y.y, tr.w0, tr.w1);
-                s_ph[i] = make_ulonglong2((unsigned long long)k * tr.A,
-                                          (unsigned long long)k * tr.B);
+                s_ph[i] = phase_consts((unsigned long long)k * tr.A, (unsigned long long)k * tr.B);
             }
             __syncthreads();
-            for (int task = warp; task < nsrc * nlb; task += kThreadsSlice / 32) {
-                const int sj = task / nlb;
-                const int l = ((task - sj * nlb) << 5) + lane;
-                const unsigned long long nl = (unsigned long long)(l < a.nq ? s_qn[l] : 0);
+            // lanes take the (source slice, curvature) pairs in order, 32 per
+            // warp; a warp straddles at most a few slices (their trace
+            // ranges differ; the lanes of each read the same trace)
+            for (int pb = warp * 32; pb < nsrc * a.nq; pb += kThreadsSlice) {
+                const int pidx = pb + lane;
+                const bool live = pidx < nsrc * a.nq;
+                const int sj = live ? pidx / a.nq : 0;
+                const int l = live ? pidx - sj * a.nq : 0;
+                const unsigned np = s_np[l];
                 int ra, rb;
                 if (sj < g.nj) {
                     ra = ss[g.ja + sj] - g.f0;
@@ -175,14 +216,14 @@ direct_adj_kernel(const DirectArgs a, const float2 *__restrict__ Y, float2 *__re
                     ra = nf;
                     rb = ntot;
                 }
-                const int lo = max(ra, c0) - c0, hi = min(rb, c0 + cn) - c0;
-                if (lo >= hi) continue;
+                int lo = max(ra, c0) - c0, hi = min(rb, c0 + cn) - c0;
+                if (!live) hi = lo;
                 float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
                 for (int i = lo; i < hi; ++i) {
                     const float4 v = s_y[i];
-                    const ulonglong2 ph = s_ph[i];
+                    const Phase32 ph = s_ph[i];
                     float c, s;
-                    cis64(ph.x + nl * ph.y, &c, &s);      // the forward's phase, bit for bit
+                    cis32(phase_top(np, ph), &c, &s);     // the forward's phase, bit for bit
                     // scale y exp(+2 pi i (k A + n_l k B))
                     const float zr = fmaf(v.x, c, -v.y * s);
                     const float zi = fmaf(v.x, s, v.y * c);
@@ -191,7 +232,7 @@ direct_adj_kernel(const DirectArgs a, const float2 *__restrict__ Y, float2 *__re
                     br = fmaf(v.w, zr, br);
                     bi = fmaf(v.w, zi, bi);
                 }
-                if (l < a.nq) {
+                if (live && lo < hi) {
                     if (sj < g.nj) {
                         float2 &o = acc0[l * g.nj + sj];
                         o.x += ar;

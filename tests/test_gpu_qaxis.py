@@ -36,10 +36,18 @@ def slowness_axis(nq):
     return pnmo.q_axis_slowness(syn.P_MIN, syn.P_MAX, nq)
 
 
-def dot_rel(gp, shape_m, shape_d, seed):
+def dot_rel(gp, op, seed):
+    """FP32 dot test on a well-conditioned pair: m random and d = L m (the
+    oracle's) plus as much noise, so <L m, d> is about |L m|^2.  For two
+    independent random vectors <L m, d> is itself a random projection, often
+    near zero, and the relative error of the test is heavy-tailed (measured
+    on every slice path: median 2-5e-7, 90th percentile 2-9e-6 over 20 random
+    pairs), which measures that cancellation rather than the adjointness."""
     rng = np.random.default_rng(seed)
-    m = rng.standard_normal(shape_m).astype(np.float32).astype(np.float64)
-    d = rng.standard_normal(shape_d).astype(np.float32).astype(np.float64)
+    m = rng.standard_normal((op.ntau, op.nq, op.ntheta)).astype(np.float32).astype(np.float64)
+    lm = ops.forward(op, m)
+    d = lm + np.sqrt(np.mean(lm * lm)) * rng.standard_normal(lm.shape)
+    d = d.astype(np.float32).astype(np.float64)
     lhs = float(np.sum(host(gp.forward(dev(m))) * d.ravel()))
     rhs = float(np.sum(host(gp.adjoint(dev(d))) * m.ravel()))
     return abs(lhs - rhs) / abs(lhs)
@@ -78,7 +86,7 @@ def test_direct_forward_adjoint_dot(name):
     d = rng.standard_normal((g.nt, g.ntr))
     assert rel(host(gp.forward(dev(m)), d.shape), ops.forward(op, m)) < TOL_OP
     assert rel(host(gp.adjoint(dev(d)), m.shape), ops.adjoint(op, d)) < TOL_OP
-    assert dot_rel(gp, m.shape, d.shape, 121) < TOL_DOT
+    assert dot_rel(gp, op, 121) < TOL_DOT
 
 
 @pytest.mark.parametrize("name", ["slowness", "centred"])
@@ -111,7 +119,7 @@ def test_direct_ragged_and_chunked_adjoint():
     d = rng.standard_normal((nt, 4000))
     assert rel(host(gp.forward(dev(m)), d.shape), ops.forward(op, m)) < TOL_OP
     assert rel(host(gp.adjoint(dev(d)), m.shape), ops.adjoint(op, d)) < TOL_OP
-    assert dot_rel(gp, m.shape, d.shape, 124) < TOL_DOT
+    assert dot_rel(gp, op, 124) < TOL_DOT
 
 
 def test_tensorcore_on_slowness_axis():
@@ -285,4 +293,4 @@ def test_config1_slowness_axis_sampled():
     mg = host(gp.adjoint(dev(g.d)), (g.ntau, g.nq, g.ntheta))
     slices = [0, 20, g.ntheta - 1]
     assert rel(mg[:, :, slices], ops.adjoint_slices(op, g.d, slices)) < TOL_OP
-    assert dot_rel(gp, m.shape, (g.nt, g.ntr), 131) < TOL_DOT
+    assert dot_rel(gp, op, 131) < TOL_DOT
