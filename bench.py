@@ -362,7 +362,7 @@ def run_ours(args):
                     "slice_adj_kernel", "c2r_r2c_kernel" if fused else "c2r_kernel"]
     if slow:
         kernel_names[1], kernel_names[4] = "direct_fwd_kernel", "direct_adj_kernel"
-    tr = None if (batch or slow) else traffic_record(names[top])
+    tr = None if batch else traffic_record(names[top] + ("@direct" if slow else ""))
     line = {
         "metric": METRIC,
         "value": round(value, 3),
