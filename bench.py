@@ -72,6 +72,25 @@ def dist_info():
     return rank, world, local
 
 
+def replica_seed(base, rank):
+    """Seed of rank's synthetic workload: every rank solves its own gather
+    (or batch) -- independent replicas, no data exchange between ranks."""
+    return base + rank
+
+
+def job_rate(local_ms, units_per_rank, world, device):
+    """Whole-job rate of independent replicas: the units all ranks processed
+    divided by the slowest rank's time (MAX over ranks; every rank returns
+    the same pair)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    return units_per_rank * world / (ms / 1e3), ms
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -216,12 +235,12 @@ def run_ours(args):
     slow = args.workload == "slowness"
     qa = None
     if batch:
-        cubes = syn.config3(seed=3 + rank)
+        cubes = syn.config3(seed=replica_seed(3, rank))
         gp = AahrtPlan.batched(cubes, autotune=True)
         d_np = np.concatenate([c.d.astype(np.float32).ravel() for c in cubes])
         iters, pairs_per_step = BATCH_ITERS, BATCH_ITERS * len(cubes)
     else:
-        g = syn.config1(seed=1 + rank)
+        g = syn.config1(seed=replica_seed(1, rank))
         if slow:
             from paper_2505_00387_gb300.plan import q_axis_slowness
             qa = q_axis_slowness(syn.P_MIN, syn.P_MAX, g.nq)
@@ -279,12 +298,7 @@ def run_ours(args):
     t_launch1 = gp.stage_times()[1]
     launches = int(sum(t_launch1[:6]) - sum(t_launch0[:6]))
 
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    pairs = args.steps * pairs_per_step * world
-    value = pairs / (total_ms / 1e3)
+    value, total_ms = job_rate(total_ms, args.steps * pairs_per_step, world, dev)
 
     # end to end: pinned host d in, pinned host m out, through the C ABI
     d_host = torch.from_numpy(d_np).pin_memory()
@@ -304,10 +318,7 @@ def run_ours(args):
     step_e2e()
     torch.cuda.synchronize()
     e2e_ms = timed(step_e2e, args.steps)
-    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = pairs / (float(te.item()) / 1e3)
+    e2e_value, _ = job_rate(e2e_ms, args.steps * pairs_per_step, world, dev)
 
     # per-stage device time over the same kind of steps (eager launches,
     # CUDA events around every stage on the launching stream)
