@@ -40,6 +40,31 @@ __device__ __forceinline__ RowRange load_rng(const RowRange *p) {
 
 constexpr int kPackBatch = 8;   // spectrum loads in flight per thread (c2r pack)
 
+// Asynchronous global -> shared copies (no registers held while in flight).
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    if (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n"); }
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Start copying nrow rows of 2P floats (row stride ld floats) into dst [row][2P].
+template <int P>
+__device__ __forceinline__ void prefetch_rows(float *dst, const float *src, int nrow, int ld) {
+    constexpr int CB = P == 1 ? 8 : 16;            // bytes per copy
+    constexpr int PER = (8 * P) / CB;              // copies per row
+    for (int idx = threadIdx.x; idx < nrow * PER; idx += blockDim.x) {
+        const int r = idx / PER, q = idx - r * PER;
+        cp_async<CB>(dst + r * 2 * P + q * (CB / 4), src + (long long)r * ld + q * (CB / 4));
+    }
+}
+
 template <int P>
 struct Acc {
     float2 v[P];
@@ -228,6 +253,11 @@ __device__ __forceinline__ void c2r_core(float2 *sm, float *sfr, const float2 *_
     }
     __syncthreads();
     block_fft<false, true, IBatch, true>(IBatch{sm, ld}, P, L, tw);
+    if (STAGE && EPI != EPI_STORE) {
+        // the epilogue's rows (d, or z) were prefetched into stg
+        cp_async_wait_all();
+        __syncthreads();
+    }
 
     // resample the synthesized columns onto the output rows, one row per thread
     for (int i = threadIdx.x; i < rs.nrows; i += blockDim.x) {
@@ -268,7 +298,8 @@ __device__ __forceinline__ void c2r_core(float2 *sm, float *sfr, const float2 *_
         } else if (EPI == EPI_RESIDUAL) {
             float dv[2 * P];
 #pragma unroll
-            for (int c = 0; c < 2 * P; ++c) dv[c] = c < nc ? __ldg(aux + o + c) : 0.f;
+            for (int c = 0; c < 2 * P; ++c)
+                dv[c] = c < nc ? (STAGE ? stg[i * 2 * P + c] : __ldg(aux + o + c)) : 0.f;
             if (STAGE) {
 #pragma unroll
                 for (int c = 0; c < 2 * P; ++c) stg[i * 2 * P + c] = c < nc ? dv[c] - g2[c] : 0.f;
@@ -291,7 +322,7 @@ __device__ __forceinline__ void c2r_core(float2 *sm, float *sfr, const float2 *_
 #pragma unroll
             for (int c = 0; c < 2 * P; ++c) {
                 mo[c] = c < nc ? mp[c] : 0.f;
-                zo[c] = c < nc ? zp[c] : 0.f;
+                zo[c] = c < nc ? (STAGE ? stg[i * 2 * P + c] : zp[c]) : 0.f;
             }
 #pragma unroll
             for (int c = 0; c < 2 * P; ++c) {
@@ -345,6 +376,12 @@ c2r_r2c_kernel(float2 *spec, const float *__restrict__ aux, FistaArgs fa,
     const ColGroup cg = groups[blockIdx.x];
     float *stg = reinterpret_cast<float *>(sm + P * ld_interleaved(1 << L));   // [row][2P]
     float *sfr = stg + nrow_mid * 2 * P;
+    // Prefetch the epilogue's state rows (the column group's slab of the
+    // column-blocked d, or of z) into stg while the spectrum is packed and
+    // transformed; the epilogue rewrites stg in place, element by element.
+    prefetch_rows<P>(stg, (EPI == EPI_RESIDUAL ? aux : fa.z) + cg.real_off, rs_syn.nrows,
+                     cg.ld_real);
+    cp_async_commit();
     c2r_core<LP, INTERP, SYN_TRANS, EPI, true>(sm, sfr, spec, nullptr, aux, fa, cg, rs_syn, n_in,
                                                tw, L, nbins, stg);
     __syncthreads();
