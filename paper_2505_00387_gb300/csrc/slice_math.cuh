@@ -66,16 +66,25 @@ __host__ __device__ __forceinline__ TapSet trace_taps(unsigned long long A,
     return t;
 }
 
-// phi at the W taps u0 + i, i < W.
+// phi at the W taps u0 + i, i < W.  The kernel is even and the taps sit
+// symmetrically about the position (z_{W-1-i}(g) = -z_i(-g)), so tap W-1-i is
+// tap i's polynomial at -g: with tap i's coefficients split into even and odd
+// powers, phi_i = E(g^2) + g O(g^2) and phi_{W-1-i} = E(g^2) - g O(g^2), one
+// pair of half-degree Horner sums per mirrored pair of taps.
 template <int W>
 __host__ __device__ __forceinline__ void es_weights(const EsPoly &P, float g, float *phi) {
-    constexpr int D = W + 1;
+    constexpr int D = W + 1;                 // polynomial degree
+    constexpr int DE = D & ~1, DO = (D - 1) | 1;   // highest even / odd power
+    const float g2 = g * g;
 #pragma unroll
-    for (int i = 0; i < W; ++i) phi[i] = P.c[D][i];
+    for (int i = 0; i < (W + 1) / 2; ++i) {
+        float e = P.c[DE][i], o = P.c[DO][i];
 #pragma unroll
-    for (int d = D - 1; d >= 0; --d) {
+        for (int d = DE - 2; d >= 0; d -= 2) e = fmaf(e, g2, P.c[d][i]);
 #pragma unroll
-        for (int i = 0; i < W; ++i) phi[i] = fmaf(phi[i], g, P.c[d][i]);
+        for (int d = DO - 2; d >= 1; d -= 2) o = fmaf(o, g2, P.c[d][i]);
+        phi[i] = fmaf(g, o, e);
+        if (W - 1 - i != i) phi[W - 1 - i] = fmaf(-g, o, e);
     }
 }
 
