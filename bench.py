@@ -235,12 +235,12 @@ def run_ours(args):
     slow = args.workload == "slowness"
     qa = None
     if batch:
-        cubes = syn.config3(seed=replica_seed(3, rank))
+        cubes = syn.cube_batch(seed=replica_seed(3, rank))
         gp = AahrtPlan.batched(cubes, autotune=True)
         d_np = np.concatenate([c.d.astype(np.float32).ravel() for c in cubes])
         iters, pairs_per_step = BATCH_ITERS, BATCH_ITERS * len(cubes)
     else:
-        g = syn.config1(seed=replica_seed(1, rank))
+        g = syn.paper_gather(seed=replica_seed(1, rank))
         if slow:
             from paper_2505_00387_gb300.plan import q_axis_slowness
             qa = q_axis_slowness(syn.P_MIN, syn.P_MAX, g.nq)
@@ -520,7 +520,7 @@ def run_reference(args):
     from oracle import ops
     from paper_2505_00387_gb300 import synthetic as syn
 
-    g = syn.config1(seed=1)
+    g = syn.paper_gather(seed=1)
     p = oracle.make_plan(**g.geom_kwargs())
     nsteps = args.steps + max(args.warmup, 3)
     frac = min(1.0, 12.0 / nsteps)
@@ -689,7 +689,7 @@ def run_shared64(args):
     from paper_2505_00387_gb300 import synthetic as syn
     from paper_2505_00387_gb300.plan import AahrtPlan
 
-    geo, _ = syn.config4(seed=replica_seed(4, rank), gathers=[])
+    geo, _ = syn.shared_batch(seed=replica_seed(4, rank), gathers=[])
     G = 64
     flush = torch.empty(256 * 1024 * 1024 // 4, device="cuda")
     res = {}

@@ -161,7 +161,7 @@ def spike_model(rng, ntau, dt, nq, q0, dq, ntheta, nspike=5, f=25.0,
 
 
 # ----------------------------------------------------------- configurations
-def config0(seed: int = 0) -> Gather:
+def small_cube(seed: int = 0) -> Gather:
     """Single CMP cube: nt=256 at 4 ms, 16x16 offset grid on [-1000,1000]^2 m,
     model 256 x 32 q x 8 azimuths holding 5 Ricker (25 Hz) spikes with 10%
     elliptical anisotropy.  The data of this case are the forward transform of
@@ -175,7 +175,7 @@ def config0(seed: int = 0) -> Gather:
                   info=dict(name="cmp-256t-16x16-32q-8az", spikes=spikes))
 
 
-def config1(seed: int = 1, ntr: int = 2000) -> Gather:
+def paper_gather(seed: int = 1, ntr: int = 2000) -> Gather:
     """Paper-scale gather: nt=1001 at 4 ms, 2000 traces uniform in a 3 km
     disc, model 100 q x 36 azimuths, data = 30 Ricker events (15-40 Hz) with
     0-20% elliptical anisotropy plus 10% Gaussian noise."""
@@ -190,10 +190,10 @@ def config1(seed: int = 1, ntr: int = 2000) -> Gather:
                   info=dict(name="cmp-1001t-2000tr-100q-36az", events=ev))
 
 
-def config3(seed: int = 3, ncube: int = 512, cubes: Optional[List[int]] = None):
+def cube_batch(seed: int = 3, ncube: int = 512, cubes: Optional[List[int]] = None):
     """Batch of CMP cubes: nt=1001 at 4 ms, fold uniform in [200, 3000],
     offsets in a 3 km disc restricted to a random azimuth sector 90-360
-    degrees wide, model 64 q x 24 azimuths, events as in config1.  Each cube
+    degrees wide, model 64 q x 24 azimuths, events as in paper_gather.  Each cube
     draws from its own seed so any subset can be regenerated alone."""
     out = []
     idx = range(ncube) if cubes is None else cubes
@@ -213,7 +213,7 @@ def config3(seed: int = 3, ncube: int = 512, cubes: Optional[List[int]] = None):
     return out
 
 
-def config4(seed: int = 4, ngather: int = 64, ntr: int = 8000,
+def shared_batch(seed: int = 4, ngather: int = 64, ntr: int = 8000,
             gathers: Optional[List[int]] = None):
     """Shared-geometry batch: ngather gathers on one geometry of 8000 traces
     in a 4 km disc, nt=2048 at 2 ms, model 200 q x 72 azimuths.  Returns

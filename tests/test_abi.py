@@ -122,7 +122,7 @@ def test_package_import_does_not_load_cuda():
         if k.endswith("synthetic"):
             continue
     mod = importlib.import_module("paper_2505_00387_gb300.synthetic")
-    assert hasattr(mod, "config0")
+    assert hasattr(mod, "small_cube")
 
 
 def test_ctypes_structs_match_the_header(tmp_path):

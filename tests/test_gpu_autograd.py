@@ -2,7 +2,7 @@
 
 * backward of d = L m is the oracle's L^T (and vice versa), <= 1e-4;
 * aahrt_fista_vjp against the oracle's reverse-mode derivative of the same
-  unrolled solve (config0 cube, FISTA and ISTA, several checkpoint spacings);
+  unrolled solve (small_cube cube, FISTA and ISTA, several checkpoint spacings);
 * at the paper-scale geometry, where the FP64 oracle is too slow for
   central differences, GPU FP32 central differences of <m_bar, m^n(d)> along
   64 random directions against <d_bar, v> (loose tolerance, FP32; steps and
@@ -22,7 +22,7 @@ pytestmark = pytest.mark.gpu
 
 @pytest.fixture(scope="module")
 def case0():
-    g = syn.config0()
+    g = syn.small_cube()
     op = oracle_plan(g)
     gp = gpu_plan(g)
     d = ops.forward(op, g.m)
@@ -121,7 +121,7 @@ def test_fista_vjp_matches_oracle_50_iterations(case0):
 
 @pytest.fixture(scope="module")
 def case1():
-    g = syn.config1()
+    g = syn.paper_gather()
     gp = gpu_plan(g)
     d = dev(g.d)
     _, info = gp.sparse_solve(d, 0.0, 0, lambda_rel=0.05)   # gamma and lambda of the data

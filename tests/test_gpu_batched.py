@@ -18,7 +18,7 @@ TOL_SOLVE = 1e-3
 
 
 def small_batch(cubes=(5, 17, 40), fold=150):
-    cs = syn.config3(ncube=len(cubes), cubes=list(cubes))
+    cs = syn.cube_batch(ncube=len(cubes), cubes=list(cubes))
     for c in cs:                 # smaller folds keep the oracle quick
         c.hx, c.hy = c.hx[:fold], c.hy[:fold]
         c.d = c.d[:, :fold]
@@ -126,7 +126,7 @@ def test_batch512_sampled_parity():
     24 azimuths): one autotuned plan; forward, adjoint and a 50-iteration
     per-cube FISTA solve checked on sampled cubes against the oracle."""
     from paper_2505_00387_gb300.plan import AahrtPlan
-    cs = syn.config3()
+    cs = syn.cube_batch()
     gp = AahrtPlan.batched(cs, autotune=True)
     r2max = max(float(np.max(c.hx ** 2 + c.hy ** 2)) for c in cs)
     folds = np.array([c.ntr for c in cs])

@@ -24,7 +24,7 @@ def wavelet(dt, center=15, n=31, f=25.0, shift=0):
 
 @pytest.fixture(scope="module")
 def case():
-    g = syn.config0()
+    g = syn.small_cube()
     op = oracle_plan(g)
     gp = gpu_plan(g)
     return g, op, gp
@@ -100,7 +100,7 @@ def test_rejects_bad_wavelet(case):
 
 
 def test_tensorcore_plan_with_wavelet():
-    g = syn.config0()
+    g = syn.small_cube()
     op = oracle_plan(g)
     G = 3
     gp = gpu_plan(g, ngather=G, precision="split_bf16")

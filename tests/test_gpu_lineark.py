@@ -22,10 +22,10 @@ def ragged():
     return syn.Gather(300, 0.004, 280, 37, q0, dq, 5, hx, hy)
 
 
-@pytest.mark.parametrize("case", ["config0", "ragged"])
+@pytest.mark.parametrize("case", ["small_cube", "ragged"])
 @pytest.mark.parametrize("sigma_q", [1.0, 2.0])
 def test_lineark_matches_oracle(case, sigma_q):
-    g = syn.config0() if case == "config0" else ragged()
+    g = syn.small_cube() if case == "small_cube" else ragged()
     op = oracle_plan(g)
     gp = gpu_plan(g, slice_interp="linear_k", sigma_q=sigma_q)
     assert gp.info.spread_width == 2
@@ -52,8 +52,8 @@ def test_lineark_matches_oracle(case, sigma_q):
 
 def test_lineark_error_against_exact_operator():
     """The GPU reproduces the method's own error (not FP32 noise): on the
-    config[0] model, linear k-interpolation at sigma_q = 1, 2, 4."""
-    g = syn.config0()
+    small-cube model, linear k-interpolation at sigma_q = 1, 2, 4."""
+    g = syn.small_cube()
     op = oracle_plan(g)
     exact = ops.forward(op, g.m)
     errs = {}
@@ -68,7 +68,7 @@ def test_lineark_error_against_exact_operator():
 
 
 def test_lineark_sparse_solve():
-    g = syn.config0()
+    g = syn.small_cube()
     op = oracle_plan(g)
     s = 2.0
     gp = gpu_plan(g, slice_interp="linear_k", sigma_q=s)
@@ -83,7 +83,7 @@ def test_lineark_sparse_solve():
 
 def test_lineark_options_checked():
     from paper_2505_00387_gb300._lib import AahrtError
-    g = syn.config0()
+    g = syn.small_cube()
     with pytest.raises(AahrtError):
         gpu_plan(g, slice_interp="linear_k", spread_width=6)
     with pytest.raises(AahrtError):

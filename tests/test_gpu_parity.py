@@ -29,20 +29,20 @@ def _cuda():
 
 
 @pytest.fixture(scope="module")
-def cfg0():
-    g = syn.config0()
+def small_case():
+    g = syn.small_cube()
     p = oracle_plan(g)
     return g, p, gpu_plan(g)
 
 
-def test_plan_matches_oracle_sampling(cfg0):
-    g, p, gp = cfg0
+def test_plan_matches_oracle_sampling(small_case):
+    g, p, gp = small_case
     assert gp.info.nfft == p.nfft and gp.info.ns == p.ns and gp.info.nbins == p.nbins
     assert abs(gp.info.ds - p.ds) <= 1e-12 * p.ds
 
 
-def test_stages_config0(cfg0):
-    g, p, gp = cfg0
+def test_stages_small_cube(small_case):
+    g, p, gp = small_case
     rng = np.random.default_rng(20)
     m = g.m
     nb = p.nbins
@@ -77,8 +77,8 @@ def test_stages_config0(cfg0):
     assert rel(m5, m5o) < 2e-6
 
 
-def test_forward_adjoint_config0(cfg0):
-    g, p, gp = cfg0
+def test_forward_adjoint_small_cube(small_case):
+    g, p, gp = small_case
     d = host(gp.forward(dev(g.m)), (p.nt, p.ntr))
     assert rel(d, ops.forward(p, g.m)) < TOL_OP
     rng = np.random.default_rng(21)
@@ -100,12 +100,12 @@ def _dot_test(gp, seed):
     return abs(a - b) / abs(a)
 
 
-def test_dot_product_config0(cfg0):
-    assert _dot_test(cfg0[2], 22) < TOL_DOT
+def test_dot_product_small_cube(small_case):
+    assert _dot_test(small_case[2], 22) < TOL_DOT
 
 
-def test_fista_config0(cfg0):
-    g, p, gp = cfg0
+def test_fista_small_cube(small_case):
+    g, p, gp = small_case
     d = ops.forward(p, g.m)
     lam = 0.05 * float(np.abs(ops.adjoint(p, d)).max())
     gamma = 0.95 / fista.power_sigma2(p, d, iters=30)
@@ -121,9 +121,9 @@ def test_fista_config0(cfg0):
     assert rel(host(mg, mi.shape), mi) < TOL_FISTA
 
 
-def test_solver_estimates_gamma_and_lambda(cfg0):
+def test_solver_estimates_gamma_and_lambda(small_case):
     """gamma from the device power iteration and lambda = 0.05 max|L^T d|."""
-    g, p, gp = cfg0
+    g, p, gp = small_case
     d = ops.forward(p, g.m)
     lam = 0.05 * float(np.abs(ops.adjoint(p, d)).max())
     sig2 = fista.power_sigma2(p, d, iters=30)
@@ -211,7 +211,7 @@ def test_plan_refuses_oversized_frame():
 
 # ---------------------------------------------------- batches and gathers
 def test_batched_cubes_match_oracle():
-    cubes = syn.config3(ncube=3, cubes=[5, 17, 40])
+    cubes = syn.cube_batch(ncube=3, cubes=[5, 17, 40])
     for c in cubes:          # smaller folds keep the oracle quick
         c.hx, c.hy = c.hx[:150], c.hy[:150]
         c.d = c.d[:, :150]
@@ -249,9 +249,9 @@ def test_shared_geometry_gathers_match_single():
 
 
 # ------------------------------------------------------------- API errors
-def test_api_rejects_bad_pointers(cfg0):
+def test_api_rejects_bad_pointers(small_case):
     from paper_2505_00387_gb300 import _lib as L
-    g, p, gp = cfg0
+    g, p, gp = small_case
     m = torch.zeros(gp.model_len + 8, device="cuda")
     d = torch.zeros(gp.data_len, device="cuda")
     with pytest.raises(L.AahrtError) as e:
@@ -275,8 +275,8 @@ def test_api_rejects_bad_pointers(cfg0):
     torch.cuda.synchronize()
 
 
-def test_profiling_counts_stages(cfg0):
-    g, p, gp = cfg0
+def test_profiling_counts_stages(small_case):
+    g, p, gp = small_case
     gp.set_profiling(True)
     d = gp.forward(dev(g.m))
     gp.adjoint(d)
@@ -288,13 +288,13 @@ def test_profiling_counts_stages(cfg0):
 
 # ------------------------------------------------- paper-scale gather
 @pytest.fixture(scope="module")
-def cfg1():
-    g = syn.config1()
+def paper_case():
+    g = syn.paper_gather()
     return g, oracle_plan(g), gpu_plan(g)
 
 
-def test_config1_sampled_forward_adjoint(cfg1):
-    g, p, gp = cfg1
+def test_paper_gather_sampled_forward_adjoint(paper_case):
+    g, p, gp = paper_case
     rng = np.random.default_rng(70)
     m = rng.standard_normal((g.ntau, g.nq, g.ntheta)).astype(np.float32).astype(np.float64)
     dg = host(gp.forward(dev(m)), (g.nt, g.ntr))
@@ -305,12 +305,12 @@ def test_config1_sampled_forward_adjoint(cfg1):
     assert rel(mg[:, :, slices], ops.adjoint_slices(p, g.d, slices)) < TOL_OP
 
 
-def test_config1_dot_product(cfg1):
-    assert _dot_test(cfg1[2], 71) < TOL_DOT
+def test_paper_gather_dot_product(paper_case):
+    assert _dot_test(paper_case[2], 71) < TOL_DOT
 
 
-def test_config1_fista_few_iterations(cfg1):
-    g, p, gp = cfg1
+def test_paper_gather_fista_few_iterations(paper_case):
+    g, p, gp = paper_case
     d = g.d
     lam = 0.05 * float(np.abs(ops.adjoint(p, d)).max())
     gamma = 0.9 / fista.power_sigma2(p, d, iters=4)

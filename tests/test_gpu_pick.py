@@ -1,6 +1,6 @@
 """GPU: the q-moment velocity pick (eq. vel_est) through the C ABI against
 the oracle, for single, batched and tensor-core (gather-fastest) plans, and
-end to end: a GPU sparse solve of config[0] data picked at each isolated
+end to end: a GPU sparse solve of small-cube data picked at each isolated
 event tracks the generator's elliptical curvature."""
 import numpy as np
 import pytest
@@ -21,7 +21,7 @@ def check(qg, wg, qo, wo):
 
 
 def test_pick_matches_oracle_single_and_batched():
-    g = syn.config0()
+    g = syn.small_cube()
     op = oracle_plan(g)
     gp = gpu_plan(g)
     rng = np.random.default_rng(100)
@@ -31,7 +31,7 @@ def test_pick_matches_oracle_single_and_batched():
     check(host(qg, qo.shape), host(wg, wo.shape), qo, wo)
 
     from paper_2505_00387_gb300.plan import AahrtPlan
-    cubes = syn.config3(ncube=2, cubes=[3, 9])
+    cubes = syn.cube_batch(ncube=2, cubes=[3, 9])
     gb = AahrtPlan.batched(cubes)
     ms = [rng.standard_normal((c.ntau, c.nq, c.ntheta)) for c in cubes]
     qg, wg = gb.pick_velocity(dev(np.concatenate([x.ravel() for x in ms])))
@@ -43,7 +43,7 @@ def test_pick_matches_oracle_single_and_batched():
 
 
 def test_pick_tensorcore_layout():
-    g = syn.config0()
+    g = syn.small_cube()
     op = oracle_plan(g)
     G = 3
     gp = gpu_plan(g, ngather=G, precision="split_bf16")
@@ -58,7 +58,7 @@ def test_pick_tensorcore_layout():
 
 
 def test_pick_after_gpu_solve_tracks_the_ellipse():
-    g = syn.config0()
+    g = syn.small_cube()
     op = oracle_plan(g)
     gp = gpu_plan(g)
     d = ops.forward(op, g.m)

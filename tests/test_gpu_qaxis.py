@@ -62,7 +62,7 @@ CASES = {
 
 
 def make_case(name, nq=32):
-    g = syn.config0()
+    g = syn.small_cube()
     c = CASES[name]
     qa = None
     if c["q"] == "slowness":
@@ -123,7 +123,7 @@ def test_direct_ragged_and_chunked_adjoint():
 
 
 def test_tensorcore_on_slowness_axis():
-    g = syn.config0()
+    g = syn.small_cube()
     qa = slowness_axis(g.nq)
     op = oracle_plan(g, q_axis=qa)
     G = 3
@@ -141,7 +141,7 @@ def test_tensorcore_on_slowness_axis():
 
 def test_batched_cubes_on_slowness_axis():
     from paper_2505_00387_gb300.plan import AahrtPlan
-    cubes = syn.config3(cubes=[1, 5, 9])
+    cubes = syn.cube_batch(cubes=[1, 5, 9])
     for c in cubes:                       # a shorter time axis keeps the oracle quick
         c.nt = c.ntau = 300
     qa = slowness_axis(cubes[0].nq)
@@ -170,7 +170,7 @@ def test_pick_on_slowness_axis():
 
 def test_explicit_axis_refusals():
     from paper_2505_00387_gb300._lib import AahrtError
-    g = syn.config0()
+    g = syn.small_cube()
     qa = slowness_axis(g.nq)
     with pytest.raises(AahrtError):
         gpu_plan(g, q_axis=qa, slice_interp="linear_k")
@@ -214,7 +214,7 @@ def test_partial_nmo_matches_oracle(interp, q_ref):
 def test_partial_nmo_layouts():
     """Gathers stored fastest (tensor-core plan) and batched cubes."""
     from paper_2505_00387_gb300.plan import AahrtPlan
-    g = syn.config0()
+    g = syn.small_cube()
     op = oracle_plan(g)
     G = 3
     gp = gpu_plan(g, ngather=G, precision="split_bf16")
@@ -224,7 +224,7 @@ def test_partial_nmo_layouts():
     for i in range(G):
         want = pnmo.partial_nmo(op, ds[i].astype(np.float32).astype(np.float64), 1.5e-7)
         assert rel(out[..., i], want) < 1e-6
-    cubes = syn.config3(cubes=[2, 3])
+    cubes = syn.cube_batch(cubes=[2, 3])
     gb = AahrtPlan.batched(cubes)
     dd = [c.d.astype(np.float32).astype(np.float64) for c in cubes]
     out = host(gb.partial_nmo(dev(np.concatenate([x.ravel() for x in dd])), -9e-8))
@@ -280,8 +280,8 @@ def test_partial_nmo_then_centred_solve():
 
 
 # ------------------------------------------------- paper-scale gather
-def test_config1_slowness_axis_sampled():
-    g = syn.config1()
+def test_paper_gather_slowness_axis_sampled():
+    g = syn.paper_gather()
     qa = slowness_axis(g.nq)
     op = oracle_plan(g, q_axis=qa)
     gp = gpu_plan(g, q_axis=qa)

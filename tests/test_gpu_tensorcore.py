@@ -44,10 +44,10 @@ def ragged_geometry():
     return syn.Gather(192, 0.004, 192, 150, q0, dq, 5, hx, hy)
 
 
-@pytest.mark.parametrize("case", ["config0", "ragged"])
+@pytest.mark.parametrize("case", ["small_cube", "ragged"])
 @pytest.mark.parametrize("G", [4, 13])
 def test_tensorcore_slice_matches_oracle(case, G):
-    g = syn.config0() if case == "config0" else ragged_geometry()
+    g = syn.small_cube() if case == "small_cube" else ragged_geometry()
     op = oracle_plan(g)
     gp = gpu_plan(g, ngather=G, precision="split_bf16")
     assert gp.info.precision == 1 and gp.info.ngather == G
@@ -88,7 +88,7 @@ def test_tensorcore_matches_fp32_path_and_empty_slice():
 
 def test_tensorcore_rejects_unsupported():
     from paper_2505_00387_gb300._lib import AahrtError
-    g = syn.config0()
+    g = syn.small_cube()
     with pytest.raises(AahrtError):
         gpu_plan(g, ngather=65, precision="split_bf16")
 
@@ -98,7 +98,7 @@ def test_shared_geometry_64_gathers_sampled():
     """64 gathers on one 8000-trace geometry (nt = 2048 at 2 ms, 200 q x 72
     azimuths): both slice paths, forward on sampled traces and adjoint on
     sampled azimuth slices of two gathers, against the oracle."""
-    geo, _ = syn.config4(gathers=[])
+    geo, _ = syn.shared_batch(gathers=[])
     G = 64
     op = oracle_plan(geo)
     rng = np.random.default_rng(83)
@@ -107,7 +107,7 @@ def test_shared_geometry_64_gathers_sampled():
     slices = [3, 40]
     shape_m = (geo.ntau, geo.nq, geo.ntheta)
     ms = {i: rng.standard_normal(shape_m) for i in sample_g}
-    _, dl = syn.config4(gathers=sample_g)
+    _, dl = syn.shared_batch(gathers=sample_g)
     ds = dict(zip(sample_g, dl))
     d_ref = {i: ops.forward_traces(op, ms[i], traces) for i in sample_g}
     m_ref = {i: ops.adjoint_slices(op, ds[i], slices) for i in sample_g}

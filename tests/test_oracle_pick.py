@@ -14,7 +14,7 @@ from paper_2505_00387_gb300 import synthetic as syn
 
 
 def test_single_and_double_cells():
-    g = syn.config0()
+    g = syn.small_cube()
     p = oracle.make_plan(**g.geom_kwargs())
     m = np.zeros((g.ntau, g.nq, g.ntheta))
     m[10, 7, 2] = -3.0
@@ -27,7 +27,7 @@ def test_single_and_double_cells():
 
 
 def test_pick_of_generated_model_is_the_ellipse():
-    g = syn.config0()
+    g = syn.small_cube()
     p = oracle.make_plan(**g.geom_kwargs())
     th = np.arange(g.ntheta) * np.pi / g.ntheta
     q_hat, _ = pick.pick(p, g.m)
@@ -42,7 +42,7 @@ def test_pick_of_generated_model_is_the_ellipse():
 
 
 def test_pick_after_sparse_solve_tracks_the_ellipse():
-    g = syn.config0()
+    g = syn.small_cube()
     p = oracle.make_plan(**g.geom_kwargs())
     d = ops.forward(p, g.m)
     gamma = 0.95 / fista.power_sigma2(p, d)

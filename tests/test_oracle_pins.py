@@ -27,7 +27,7 @@ def tiny_plan(ntr=12, nt=96, dt=0.008, nq=6, ntheta=4, seed=0, **kw):
 # ------------------------------------------------------------ plan (eq. q3)
 @pytest.mark.parametrize("cfg", [0, 1])
 def test_plan_sampling_no_wrap(cfg):
-    g = syn.config0() if cfg == 0 else syn.config1()
+    g = syn.small_cube() if cfg == 0 else syn.paper_gather()
     p = oracle.make_plan(**g.geom_kwargs())
     assert p.nfft & (p.nfft - 1) == 0
     assert p.nfft >= 2.0 * p.nt * (1.0 + p.rho)
@@ -307,8 +307,8 @@ def test_zero_curvature_and_single_slice():
 
 
 # ------------------------------------------------------------ adjoint (O5)
-def test_dot_product_fp64_config0():
-    g = syn.config0()
+def test_dot_product_fp64_small_cube():
+    g = syn.small_cube()
     p = oracle.make_plan(**g.geom_kwargs())
     m, d = syn.random_pair(11, g)
     lhs = np.sum(ops.forward(p, m) * d)

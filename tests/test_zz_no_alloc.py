@@ -26,7 +26,7 @@ def plan():
     build.build()
     from paper_2505_00387_gb300 import synthetic as syn
     from paper_2505_00387_gb300.plan import AahrtPlan
-    g = syn.config0()
+    g = syn.small_cube()
     return g, AahrtPlan(**g.geom_kwargs())
 
 
@@ -53,7 +53,7 @@ def test_noalloc_rejects_plans_beyond_its_scratch():
     from paper_2505_00387_gb300.plan import AahrtPlan
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    g = syn.config1()
+    g = syn.paper_gather()
     gp = AahrtPlan(**g.geom_kwargs())
     need = 8 * (gp.info.xspec_len + gp.info.yspec_len) + 256
     assert need > (16 << 20)
