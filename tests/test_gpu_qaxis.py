@@ -8,7 +8,8 @@ same seeded inputs.
   traces do not fit one staging pass;
 * the tensor-core contraction on a uniform-slowness axis (3 gathers) and a
   batched plan of cubes with it;
-* the q-moment pick on the explicit axis;
+* the q-moment pick on the explicit axis; the wavelet, the unrolled-solve
+  derivative and the allocation-free forward on a direct-sum plan;
 * partial NMO: forward and transpose (Keys and linear) against the oracle,
   muted zones, the gathers-fastest and batched layouts, and the pipeline
   partial NMO -> solve on the centred axis of eq. q3;
@@ -182,6 +183,42 @@ def test_explicit_axis_refusals():
     with pytest.raises(AahrtError):
         gp.velocity_scan_grid(dev(np.zeros((g.nt, g.ntr))),
                               (16, 16, -1000.0, 2000.0 / 15, -1000.0, 2000.0 / 15))
+
+
+def test_direct_with_wavelet_vjp_and_noalloc():
+    """The direct-sum plan composes with the rest of the operator pair: the
+    deconvolutive W L (eq. DecRT) against the oracle on the same axis, the
+    unrolled-solve derivative (linear case: the transpose identity), and the
+    allocation-free forward (bitwise the plan's forward)."""
+    from oracle import decon
+    from paper_2505_00387_gb300 import _lib as L
+    g, op, gp = make_case("slowness")
+    t = (np.arange(31) - 15) * g.dt
+    w = syn.ricker(t, 25.0).astype(np.float32)
+    wf = w.astype(np.float64)
+    rng = np.random.default_rng(132)
+    m = rng.standard_normal((g.ntau, g.nq, g.ntheta)).astype(np.float32).astype(np.float64)
+    gp.set_wavelet(w, 15)
+    try:
+        dg = host(gp.forward(dev(m)), (g.nt, g.ntr))
+        assert rel(dg, decon.forward(op, m, wf, 15)) < TOL_OP
+        d = decon.forward(op, m, wf, 15)
+        gamma = float(np.float32(0.95 / fista.power_sigma2(
+            op, d, op=(lambda x: decon.forward(op, x, wf, 15),
+                       lambda r: decon.adjoint(op, r, wf, 15)))))
+        m_bar = rng.standard_normal(m.shape)
+        m_n, d_bar = gp.fista_vjp(dev(d), dev(m_bar), 0.0, gamma, 6, checkpoint=2)
+        lhs = float(np.sum(host(m_n) * m_bar.ravel()))
+        rhs = float(np.sum(host(d_bar) * d.ravel()))
+        assert abs(lhs - rhs) <= 1e-4 * (abs(lhs) + abs(rhs))
+        mm = dev(m)
+        d_ref = gp.forward(mm).clone()
+        d_na = torch.full_like(d_ref, float("nan"))
+        L.aahrt_forward_noalloc(gp.handle, mm.data_ptr(), d_na.data_ptr())
+        torch.cuda.synchronize()
+        assert torch.equal(d_ref, d_na)
+    finally:
+        gp.set_wavelet(None, 0)
 
 
 # ------------------------------------------------------------- partial NMO
