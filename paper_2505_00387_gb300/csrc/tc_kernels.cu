@@ -404,13 +404,14 @@ slice_adj_tc_kernel(const TcArgs a, const float2 *__restrict__ Yh, float2 *__res
                     }
                 }
             }
-            // B: rows (part, g), K = 32 traces x (Re, Im)
-            for (int u = tid; u < 4 * Gp; u += kTcThreads) {
-                const int g = u % Gp, tb = u / Gp;
-                float vr[16], vi[16];
+            // B: rows (part, g), K = 32 traces x (Re, Im); one unit is one
+            // 16-byte chunk (4 traces) of a row pair, so 8 Gp units
+            for (int u = tid; u < 8 * Gp; u += kTcThreads) {
+                const int g = u % Gp, tq = u / Gp;
+                float vr[8], vi[8];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int p = 32 * c + 8 * tb + i;
+                for (int i = 0; i < 4; ++i) {
+                    const int p = 32 * c + 4 * tq + i;
                     float2 y = make_float2(0.f, 0.f);
                     if (p < ntot && g < a.G)
                         y = __ldg(p < n1 ? Ya + (long long)p * a.G + g
@@ -420,19 +421,13 @@ slice_adj_tc_kernel(const TcArgs a, const float2 *__restrict__ Yh, float2 *__res
                     vi[2 * i] = y.y;
                     vi[2 * i + 1] = y.x;
                 }
-                uint4 h0, lo0, h1, lo1;
-                split8(vr, &h0, &lo0);
-                split8(vr + 8, &h1, &lo1);
-                st_chunk(bhi, g, 2 * tb, h0);
-                st_chunk(bhi, g, 2 * tb + 1, h1);
-                st_chunk(blo, g, 2 * tb, lo0);
-                st_chunk(blo, g, 2 * tb + 1, lo1);
-                split8(vi, &h0, &lo0);
-                split8(vi + 8, &h1, &lo1);
-                st_chunk(bhi, Gp + g, 2 * tb, h0);
-                st_chunk(bhi, Gp + g, 2 * tb + 1, h1);
-                st_chunk(blo, Gp + g, 2 * tb, lo0);
-                st_chunk(blo, Gp + g, 2 * tb + 1, lo1);
+                uint4 h, lo;
+                split8(vr, &h, &lo);
+                st_chunk(bhi, g, tq, h);
+                st_chunk(blo, g, tq, lo);
+                split8(vi, &h, &lo);
+                st_chunk(bhi, Gp + g, tq, h);
+                st_chunk(blo, Gp + g, tq, lo);
             }
             fence_async_smem();
             __syncthreads();
