@@ -422,9 +422,19 @@ int aahrt_forward_noalloc(aahrt_plan *plan, const float *m, float *d, void *stre
 
 /* Synchronises the plan's device and reports device-side failures of its
  * kernels since the last call: AAHRT_ERR_TIMEOUT if a tensor-core kernel
- * gave up waiting for its matrix unit (its output is then incomplete), else
- * AAHRT_OK.  The flag is cleared. */
+ * gave up waiting for its matrix unit (every such wait is bounded by 1 s of
+ * device time; the kernel then releases its tensor memory and returns, its
+ * output incomplete), else AAHRT_OK.  The flag is cleared. */
 int aahrt_plan_status(aahrt_plan *plan);
+
+/* Test hook for the failure path above: while on, the plan's tensor-core
+ * kernels issue no matrix operations, so their bounded waits run out (after
+ * 20 ms of device time instead of the normal 1 s limit), the kernels record
+ * the timeout, release their tensor memory and return, and the next
+ * aahrt_plan_status reports AAHRT_ERR_TIMEOUT.  Outputs computed meanwhile
+ * are invalid.  Plans of other precisions get AAHRT_ERR_UNSUPPORTED.  Not for
+ * production use. */
+int aahrt_plan_test_stall(aahrt_plan *plan, int on);
 
 const char *aahrt_status_string(int status);
 const char *aahrt_last_error(void);

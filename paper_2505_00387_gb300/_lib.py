@@ -99,6 +99,7 @@ _SIGS = {
     "aahrt_velocity_scan_grid": (c_int, [c_void_p, POINTER(aahrt_grid), c_void_p, c_void_p,
                                          c_void_p]),
     "aahrt_forward_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "aahrt_plan_test_stall": (c_int, [c_void_p, c_int]),
     "aahrt_q_axis_slowness": (c_int, [c_double, c_double, c_int, POINTER(c_double)]),
     "aahrt_nq_required": (c_int, [c_double, c_double, c_double, POINTER(c_int)]),
     "aahrt_partial_nmo": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_int, c_void_p]),
@@ -209,6 +210,10 @@ def aahrt_q_from_slowness(pmin: float, pmax: float, nq: int):
     check(load().aahrt_q_from_slowness(pmin, pmax, nq, ctypes.byref(q0), ctypes.byref(dq)),
           "aahrt_q_from_slowness")
     return q0.value, dq.value
+
+
+def aahrt_plan_test_stall(h, on: bool):
+    check(load().aahrt_plan_test_stall(h, int(bool(on))), "aahrt_plan_test_stall")
 
 
 def aahrt_q_axis_slowness(pmin: float, pmax: float, nq: int):

@@ -839,6 +839,21 @@ int aahrt_plan_status(aahrt_plan *plan) {
     return AAHRT_OK;
 }
 
+int aahrt_plan_test_stall(aahrt_plan *plan, int on) {
+    if (!plan) return set_error(AAHRT_ERR_INVALID_ARG, "plan is NULL");
+    Plan &p = *plan->p;
+    if (p.precision != AAHRT_PRECISION_SPLIT_BF16)
+        return set_error(AAHRT_ERR_UNSUPPORTED, "only tensor-core plans wait on matrix operations");
+    if (on != 0 && on != 1) return set_error(AAHRT_ERR_INVALID_ARG, "on must be 0 or 1");
+    p.tc_stall = on != 0;
+    if (p.gexec) {                 // a captured solve holds the old kernel arguments
+        cudaGraphExecDestroy(p.gexec);
+        p.gexec = nullptr;
+        p.gkey.clear();
+    }
+    return AAHRT_OK;
+}
+
 const char *aahrt_status_string(int status) {
     switch (status) {
         case AAHRT_OK: return "success";

@@ -179,6 +179,7 @@ struct Plan {
     long long pn_ntr = 0;
     int tc_gp = 0;                 // gathers padded to a multiple of 8
     int4 *tc_tiles = nullptr;      // forward row tiles {slice, first, end, 0}
+    bool tc_stall = false;         // test hook: tensor-core kernels issue no MMAs
     int tc_ntiles = 0;
     // deconvolutive operator: wavelet convolved with every trace in time
     float *wav = nullptr;          // nw samples (device)

@@ -49,6 +49,8 @@ struct TcArgs {
     int *err;
     long long total;
     const long long *__restrict__ qn;     // explicit axis: q_l = q_c + qn[l] eps, else null
+    unsigned long long wait_ns;           // device time a wait may take before giving up
+    int stall;                            // test hook: issue no matrix operations
     int ntiles, nbins, nq, ntheta, G, Gp, ntr, cq;
     float scale;
 };
@@ -155,9 +157,9 @@ __device__ __forceinline__ void tc_begin(TcState &s, uint64_t *mbar, uint32_t *t
 }
 
 // wait for the latest commit on buffer b
-__device__ __forceinline__ void tc_wait(TcState &s, int b, int *err) {
+__device__ __forceinline__ void tc_wait(TcState &s, int b, int *err, unsigned long long ns) {
     if (s.ncommit[b] == 0 || s.failed) return;
-    if (!mbar_wait(s.mbar[b], (s.ncommit[b] - 1) & 1u, kTcWait)) {
+    if (!mbar_wait(s.mbar[b], (s.ncommit[b] - 1) & 1u, kTcWait, ns)) {
         s.failed = true;
         if ((threadIdx.x & 31) == 0) atomicExch(err, 1);
     }
@@ -184,10 +186,10 @@ __device__ __forceinline__ long long tc_next(const TcArgs &a, TcState &s, long l
 
 // After a timeout: give the MMAs already issued a bounded chance to finish
 // before the TMEM is released.
-__device__ __forceinline__ void tc_drain(TcState &s) {
+__device__ __forceinline__ void tc_drain(TcState &s, unsigned long long ns) {
     if (!s.failed) return;
     for (int b = 0; b < 2; ++b)
-        if (s.ncommit[b] > 0) mbar_wait(s.mbar[b], (s.ncommit[b] - 1) & 1u, kTcWait);
+        if (s.ncommit[b] > 0) mbar_wait(s.mbar[b], (s.ncommit[b] - 1) & 1u, kTcWait, ns);
 }
 
 // ------------------------------------------------------------- forward
@@ -221,7 +223,7 @@ slice_fwd_tc_kernel(const TcArgs a, const float2 *__restrict__ X, float2 *__rest
 
         for (int c = 0; c < nch; ++c) {
             const int b = c & 1;
-            if (c >= 2) tc_wait(s, b, a.err);
+            if (c >= 2) tc_wait(s, b, a.err, a.wait_ns);
             unsigned char *ahi = sm + b * stage_bytes, *alo = ahi + kTileA;
             unsigned char *bhi = alo + kTileA, *blo = bhi + bbytes;
             // A: E[h][l] for 128 traces x 32 q samples, (Re, Im) interleaved
@@ -282,7 +284,7 @@ slice_fwd_tc_kernel(const TcArgs a, const float2 *__restrict__ X, float2 *__rest
             }
             fence_async_smem();
             __syncthreads();
-            if (tid == 0) {
+            if (tid == 0 && !a.stall) {
                 fence_after_sync();
                 const uint32_t a_hi = smem_u32(ahi), a_lo = smem_u32(alo);
                 const uint32_t b_hi = smem_u32(bhi), b_lo = smem_u32(blo);
@@ -297,7 +299,7 @@ slice_fwd_tc_kernel(const TcArgs a, const float2 *__restrict__ X, float2 *__rest
             }
             s.ncommit[b]++;
         }
-        tc_wait(s, (nch - 1) & 1, a.err);
+        tc_wait(s, (nch - 1) & 1, a.err, a.wait_ns);
         fence_after_sync();
         if (s.failed) continue;
 
@@ -327,7 +329,7 @@ slice_fwd_tc_kernel(const TcArgs a, const float2 *__restrict__ X, float2 *__rest
             }
         }
     }
-    tc_drain(s);
+    tc_drain(s, a.wait_ns);
     tc_end(s);
 }
 
@@ -365,7 +367,7 @@ slice_adj_tc_kernel(const TcArgs a, const float2 *__restrict__ Yh, float2 *__res
 
         for (int c = 0; c < nch; ++c) {
             const int b = c & 1;
-            if (c >= 2) tc_wait(s, b, a.err);
+            if (c >= 2) tc_wait(s, b, a.err, a.wait_ns);
             unsigned char *st0 = sm + b * stage_bytes;
             unsigned char *bhi = st0 + 4 * kTileA, *blo = bhi + bbytes;
             // A: w conj(E)[l][h], rows l (two M-tiles), K = 32 traces
@@ -431,7 +433,7 @@ slice_adj_tc_kernel(const TcArgs a, const float2 *__restrict__ Yh, float2 *__res
             }
             fence_async_smem();
             __syncthreads();
-            if (tid == 0) {
+            if (tid == 0 && !a.stall) {
                 fence_after_sync();
                 const uint32_t b_hi = smem_u32(bhi), b_lo = smem_u32(blo);
                 for (int mt = 0; mt < nmt; ++mt) {
@@ -452,7 +454,7 @@ slice_adj_tc_kernel(const TcArgs a, const float2 *__restrict__ Yh, float2 *__res
             }
             s.ncommit[b]++;
         }
-        if (nch > 0) tc_wait(s, (nch - 1) & 1, a.err);
+        if (nch > 0) tc_wait(s, (nch - 1) & 1, a.err, a.wait_ns);
         fence_after_sync();
         if (s.failed) continue;
 
@@ -480,7 +482,7 @@ slice_adj_tc_kernel(const TcArgs a, const float2 *__restrict__ Yh, float2 *__res
             }
         }
     }
-    tc_drain(s);
+    tc_drain(s, a.wait_ns);
     tc_end(s);
 }
 
@@ -502,6 +504,8 @@ static TcArgs tc_args(const Plan &p, bool adjoint, int *counter) {
     a.ntr = p.ntr[0];
     a.cq = p.cq;
     a.qn = p.qexplicit ? p.qn : nullptr;
+    a.stall = p.tc_stall ? 1 : 0;
+    a.wait_ns = p.tc_stall ? 20000000ull : 1000000000ull;   // 20 ms under the test hook, else 1 s
     a.scale = (float)(1.0 / p.nfft);
     return a;
 }

@@ -102,7 +102,17 @@ __device__ __forceinline__ void mbar_fence_init() {
 
 // Wait for the phase with the given parity to complete; gives up after
 // `limit` polls and returns false (the caller records the timeout).
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32_t limit) {
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the mbarrier phase of the given parity; gives up (false) after
+// timeout_ns of device time or `limit` polls, whichever comes first.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32_t limit,
+                                          unsigned long long timeout_ns) {
+    const unsigned long long t0 = globaltimer_ns();
     for (uint32_t i = 0; i < limit; ++i) {
         uint32_t done;
         asm volatile(
@@ -111,6 +121,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32
             "selp.u32 %0, 1, 0, p;\n\t}\n"
             : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
         if (done) return true;
+        if ((i & 63u) == 63u && globaltimer_ns() - t0 > timeout_ns) return false;
     }
     return false;
 }

@@ -147,3 +147,34 @@ def test_shared_geometry_64_gathers_sampled():
         del gp
         torch.cuda.empty_cache()
     print("relative L2 vs FP64 oracle (forward, adjoint):", errs)
+
+
+def test_bounded_wait_reports_timeout_and_recovers():
+    """Failure path of the tensor-core kernels without a GPU fault: under the
+    test hook no matrix operation is issued, so every bounded wait runs out
+    (20 ms of device time); the kernels flag it, release their tensor memory
+    and return, aahrt_plan_status reports AAHRT_ERR_TIMEOUT, and the plan
+    computes the same result as before once the hook is off."""
+    from paper_2505_00387_gb300 import _lib as L
+    g = syn.small_cube()
+    G = 3
+    gp = gpu_plan(g, ngather=G, precision="split_bf16")
+    rng = np.random.default_rng(140)
+    m = dev(interleave([rng.standard_normal(g.m.shape) for _ in range(G)]))
+    d0 = gp.forward(m).clone()
+    gp.status()
+    L.aahrt_plan_test_stall(gp.handle, True)
+    try:
+        gp.forward(m)
+        with pytest.raises(L.AahrtError) as err:
+            gp.status()
+        assert err.value.status == L.AAHRT_ERR_TIMEOUT
+        gp.status()                              # the flag was cleared
+    finally:
+        L.aahrt_plan_test_stall(gp.handle, False)
+    d1 = gp.forward(m)
+    gp.status()
+    assert torch.equal(d0, d1)
+    fp = gpu_plan(g)                             # FP32 plans have no such wait
+    with pytest.raises(L.AahrtError):
+        L.aahrt_plan_test_stall(fp.handle, True)
