@@ -134,7 +134,8 @@ typedef struct {
     double sigma_t;     /* FFT frame oversampling of the time axis; 0 = 2 */
     double fmax;        /* highest kept stretched frequency in 1/s^2; 0 = all */
     int time_pairs;     /* column pairs per time-kernel block (1, 2, 4 or 8);
-                           0 = automatic (8192 / Nfft, clamped) */
+                           0 = automatic (8192 / Nfft clamped to [2, 8] up to
+                           Nfft = 8192, 1 beyond) */
     int autotune;       /* 1: pick spread_width, theta_group and time_pairs
                            at plan creation (see aahrt_plan_create); fields
                            set explicitly above are kept */

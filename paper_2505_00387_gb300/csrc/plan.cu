@@ -341,7 +341,19 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
     if (p->fmax > 0.0)
         p->kmax = std::min(p->kmax, (int)std::floor(p->fmax * p->nfft * p->ds));
     p->nbins = p->kmax + 1;
-    p->pairs = opts.time_pairs > 0 ? opts.time_pairs : std::max(1, std::min(8, 8192 / p->nfft));
+    // column pairs per time block: 8192 / Nfft, at least 2 up to Nfft = 8192
+    // (two pairs write whole 32-byte sectors of gathers-fastest spectra) when
+    // their shared memory fits the device, 1 beyond
+    p->pairs = opts.time_pairs > 0 ? opts.time_pairs
+                                   : (p->nfft <= 8192 ? std::max(2, std::min(8, 8192 / p->nfft)) : 1);
+    if (opts.time_pairs == 0 && p->pairs == 2 && 8192 / p->nfft < 2) {
+        int optin = 0;
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+        const size_t fftb2 = 2 * (size_t)ld_interleaved(p->nfft) * sizeof(float2);
+        const size_t need = fftb2 + (size_t)std::max(p->ntau, p->nt) * 4 * sizeof(float) +
+                            (size_t)std::max(p->ns, p->nt) * sizeof(float);
+        if (need > (size_t)optin) p->pairs = 1;
+    }
     p->lp = ilog2(p->pairs);
 
     // ----------------------------------------------------- q spreading
