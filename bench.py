@@ -288,12 +288,17 @@ def run_ours(args):
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
-        return sum(a.elapsed_time(b) for a, b in ev)
+        per_step.clear()
+        per_step.extend(a.elapsed_time(b) for a, b in ev)
+        return sum(per_step)
+
+    per_step = []
 
     t_launch0 = gp.stage_times()[1]
     sampler = ClockSampler(local)
     sampler.start()
     total_ms = timed(step, args.steps)
+    step_median_ms = statistics.median(per_step)
     clocks = sampler.stop()
     t_launch1 = gp.stage_times()[1]
     launches = int(sum(t_launch1[:6]) - sum(t_launch0[:6]))
@@ -382,6 +387,7 @@ def run_ours(args):
         "steps": args.steps,
         "warmup": max(args.warmup, 3),
         "ms_per_step": round(total_ms / args.steps, 4),
+        "ms_per_step_median": round(step_median_ms, 4),
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
