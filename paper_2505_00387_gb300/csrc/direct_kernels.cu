@@ -25,6 +25,7 @@
 #include <algorithm>
 
 #include "internal.cuh"
+#include "slice_math.cuh"
 
 namespace aahrt {
 
@@ -40,26 +41,6 @@ struct DirectArgs {
     int nbins, nq, ntheta, ngroup, tgroup, chunk;
     float scale;
 };
-
-// The top 32 bits of the phase k A + n_l k B (mod 2^64) from 32-bit
-// multiplies: with n' = n_l + 2^31 (0 <= n' < 2^32 since |n_l| <= 2^30) and
-// A' = k A - 2^31 k B, the sum is A' + n' k B, whose top word is
-//   hi(A') + lo(n' hi(kB)) + hi(n' lo(kB))
-// up to the carry of the low words (at most 2^-32 cycle, dropped).  The
-// forward and the adjoint evaluate it through the same code, so their phases
-// agree bit for bit.
-struct Phase32 {
-    unsigned hiA, bh, bl, pad;
-};
-
-__device__ __forceinline__ Phase32 phase_consts(unsigned long long kA, unsigned long long kB) {
-    const unsigned long long ap = kA - (kB << 31);
-    return Phase32{(unsigned)(ap >> 32), (unsigned)(kB >> 32), (unsigned)kB, 0u};
-}
-
-__device__ __forceinline__ unsigned phase_top(unsigned np, const Phase32 &p) {
-    return __umulhi(np, p.bl) + (np * p.bh + p.hiA);
-}
 
 // (cos, sin) of 2 pi t 2^-32 for a signed fraction t of a cycle
 __device__ __forceinline__ void cis32(unsigned t, float *c, float *s) {

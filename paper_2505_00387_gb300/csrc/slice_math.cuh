@@ -132,4 +132,32 @@ inline void fit_es_poly(int W, double beta, EsPoly *P) {
     }
 }
 
+// Top 32 bits of a direct-sum phase k A + n_l k B (0.64 fixed point, mod 2^64)
+// from 32-bit multiplies: with n' = n_l + 2^31 (0 <= n' < 2^32 since
+// |n_l| <= 2^30) and A' = k A - 2^31 k B, the sum is A' + n' k B, whose top
+// word is hi(A') + lo(n' hi(kB)) + hi(n' lo(kB)) up to the carry of the low
+// words (at most 2^-32 cycle, dropped).  The forward and the adjoint evaluate
+// it through the same code, so their phases agree bit for bit.
+struct Phase32 {
+    unsigned hiA, bh, bl, pad;
+};
+
+__host__ __device__ __forceinline__ Phase32 phase_consts(unsigned long long kA,
+                                                         unsigned long long kB) {
+    const unsigned long long ap = kA - (kB << 31);
+    return Phase32{(unsigned)(ap >> 32), (unsigned)(kB >> 32), (unsigned)kB, 0u};
+}
+
+__host__ __device__ __forceinline__ unsigned umulhi32(unsigned a, unsigned b) {
+#ifdef __CUDA_ARCH__
+    return __umulhi(a, b);
+#else
+    return (unsigned)(((unsigned long long)a * b) >> 32);
+#endif
+}
+
+__host__ __device__ __forceinline__ unsigned phase_top(unsigned np, const Phase32 &p) {
+    return umulhi32(np, p.bl) + (np * p.bh + p.hiA);
+}
+
 }  // namespace aahrt

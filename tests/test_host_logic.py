@@ -84,3 +84,26 @@ def test_curvature_axis_helpers_match_oracle():
         L.aahrt_nq_required(-1.0, 1.0, 1.0)
     with pytest.raises(L.AahrtError):
         L.aahrt_q_axis_slowness(1e-4, float("nan"), 4)
+
+
+def test_direct_sum_phase_top_word(tmp_path):
+    """The direct sum's phase from 32-bit multiplies (offset curvature index,
+    dropped low-word carry) equals the exact top word of k A + n k B
+    (mod 2^64) or falls short of it by one unit (2^-32 cycle), for curvature
+    indices up to the axis quantisation's 2^30."""
+    exe = str(tmp_path / "phase32_harness")
+    _compile(os.path.join(HERE, "host", "phase32_harness.cpp"), exe)
+    rng = np.random.default_rng(5)
+    cases = []
+    for _ in range(2000):
+        kA = int(rng.integers(0, 2**63)) * 2 + int(rng.integers(0, 2))
+        kB = int(rng.integers(0, 2**63)) * 2 + int(rng.integers(0, 2))
+        n = int(rng.integers(-2**30, 2**30 + 1))
+        cases.append((kA, kB, n))
+    cases += [(0, 0, 0), (2**64 - 1, 2**64 - 1, 2**30), (2**63, 1, -2**30), (12345, 2**32, -1)]
+    inp = "\n".join("%d %d %d" % c for c in cases) + "\n"
+    r = subprocess.run([exe], input=inp, capture_output=True, text=True, check=True)
+    for (kA, kB, n), line in zip(cases, r.stdout.strip().splitlines()):
+        top, exact = (int(v) for v in line.split())
+        assert exact == ((kA + n * kB) % 2**64) >> 32
+        assert (exact - top) % 2**32 in (0, 1)
