@@ -109,9 +109,24 @@ def test_batched_rejects_mismatched_axes(lib):
 
 
 def test_null_plan_calls(lib):
-    assert lib.aahrt_forward(None, None, None, None) == L.AAHRT_ERR_INVALID_ARG
-    assert lib.aahrt_adjoint(None, None, None, None) == L.AAHRT_ERR_INVALID_ARG
-    assert lib.aahrt_plan_query(None, None) == L.AAHRT_ERR_INVALID_ARG
+    bad = L.AAHRT_ERR_INVALID_ARG
+    assert lib.aahrt_forward(None, None, None, None) == bad
+    assert lib.aahrt_adjoint(None, None, None, None) == bad
+    assert lib.aahrt_plan_query(None, None) == bad
+    # every entry point that takes a plan refuses a NULL one before touching
+    # a device
+    assert lib.aahrt_sparse_solve(None, None, 0.0, 1, None, None, None, None) == bad
+    assert lib.aahrt_apply_stage(None, 0, None, None, None) == bad
+    assert lib.aahrt_fista_vjp(None, None, None, 0.0, 1.0, 1, 0, 0, None, None, None) == bad
+    assert lib.aahrt_plan_set_wavelet(None, None, 0, 0) == bad
+    assert lib.aahrt_pick_velocity(None, None, None, None, None) == bad
+    assert lib.aahrt_velocity_scan_grid(None, None, None, None, None) == bad
+    assert lib.aahrt_forward_noalloc(None, None, None, None) == bad
+    assert lib.aahrt_partial_nmo(None, None, None, 1e-7, 0, None) == bad
+    assert lib.aahrt_plan_test_stall(None, 1) == bad
+    assert lib.aahrt_plan_set_profiling(None, 1) == bad
+    assert lib.aahrt_plan_stage_times(None, None, None) == bad
+    assert lib.aahrt_plan_status(None) == bad
     lib.aahrt_plan_destroy(None)
 
 
