@@ -344,13 +344,96 @@ def test_soft_threshold_piecewise():
         np.testing.assert_allclose(fista.soft(x, t), checks.soft_piecewise(x, t), atol=1e-15)
 
 
-def test_momentum_schedule_closed_form():
-    b = fista.momentum_schedule(5)
-    t = [1.0]
-    for _ in range(5):
-        t.append((1 + np.sqrt(1 + 4 * t[-1] ** 2)) / 2)
-    np.testing.assert_allclose(b, [(t[i] - 1) / t[i + 1] for i in range(5)])
+class _Diag:
+    """A diagonal operator on a 1 x 1 x n model, recording the points the
+    solver evaluates L at (the extrapolated iterates z^k)."""
+
+    def __init__(self, a):
+        self.a = np.asarray(a, np.float64)
+        self.ntau, self.nq, self.ntheta = 1, 1, len(a)
+        self.seen = []
+
+    def fwd(self, m):
+        self.seen.append(np.array(m, np.float64).ravel())
+        return self.a * m.ravel()
+
+    def adj(self, r):
+        return (self.a * r).reshape(1, 1, -1)
+
+
+def _golden_fista():
+    rows = []
+    with open(os.path.join(GOLDEN, "fista_diagonal.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                v = [float(x) for x in line.split()]
+                rows.append((int(v[0]), v[1], np.array(v[2:6]), np.array(v[6:10])))
+    return rows
+
+
+def test_fista_iterates_hand_worked():
+    """The first four FISTA iterates m^k and extrapolated points z^k of a
+    decoupled problem, worked by hand from Beck and Teboulle's recursion
+    (tests/golden/fista_diagonal.txt): pins the weight (t_k - 1)/t_{k+1}, the
+    index of t, the extrapolation from m^k, the step and the threshold."""
+    rows = _golden_fista()
+    d = np.array([3.0, 4.0, -4.8, -0.4])
+    for k, _, m_want, _ in rows:
+        op = _Diag([2.0, 1.0, 1.0, 1.0])
+        m = fista.solve(op, d, 2.0, k, 0.25, op=(op.fwd, op.adj))
+        np.testing.assert_allclose(m.ravel(), m_want, rtol=0, atol=1e-14)
+    # the solver evaluates the gradient at z^0 .. z^3
+    op = _Diag([2.0, 1.0, 1.0, 1.0])
+    fista.solve(op, d, 2.0, 4, 0.25, op=(op.fwd, op.adj))
+    np.testing.assert_allclose(op.seen[0], 0.0, atol=0)
+    for (k, _, _, z_want), z_got in zip(rows[:3], op.seen[1:]):
+        np.testing.assert_allclose(z_got, z_want, rtol=0, atol=1e-14)
+    # ISTA on the same problem: z^k = m^k, so m^{k+1} = 3 m^k / 4 + 1/2 in
+    # coordinate 1 (1/2, 7/8, 37/32, ...)
+    op = _Diag([2.0, 1.0, 1.0, 1.0])
+    m = fista.solve(op, d, 2.0, 3, 0.25, momentum=False, op=(op.fwd, op.adj))
+    np.testing.assert_allclose(m.ravel(), [1.0, 37 / 32, -1.4 * 37 / 32, 0.0], atol=1e-15)
+
+
+def test_momentum_schedule_quadratic_identity():
+    """t_{k+1} is the positive root of t^2 - t - t_k^2 = 0 and t_0 = 1, so
+    beta_0 = 0, t_1 is the golden ratio and, recovering t_{k+1} = (t_k - 1) /
+    beta_k, every later pair satisfies t_{k+1}^2 - t_{k+1} = t_k^2; Beck and
+    Teboulle's bound t_k >= (k + 2)/2 holds (their Lemma 4.3)."""
+    b = fista.momentum_schedule(40)
     assert b[0] == 0.0
+    t = [1.0, (1.0 + np.sqrt(5.0)) / 2.0]
+    for k in range(1, 40):
+        t.append((t[k] - 1.0) / b[k])
+    t = np.array(t)
+    np.testing.assert_allclose(t[1:] ** 2 - t[1:], t[:-1] ** 2, rtol=1e-12)
+    assert np.all(t >= (np.arange(len(t)) + 2) / 2.0 - 1e-12)
+    rows = _golden_fista()
+    np.testing.assert_allclose(t[1:5], [r[1] for r in rows], rtol=1e-15)
+
+
+def test_fista_rate_bound():
+    """Beck and Teboulle's Theorem 4.4 on a small AAHRT problem: with a step
+    gamma <= 1/||L||^2, F(m^k) - F* <= 2 ||m^0 - m*||^2 / (gamma (k + 1)^2)
+    for every k, F of eq. cost1.  F* and m* come from a long run (F* from a
+    run is an upper bound of the minimum, so the check is, if anything,
+    looser than the theorem)."""
+    p = tiny_plan(ntr=10, nt=64, nq=5, ntheta=3, seed=5)
+    rng = np.random.default_rng(21)
+    d = rng.standard_normal((p.nt, p.ntr))
+    sig2 = fista.power_sigma2(p, d, iters=200)
+    gamma = 0.9 / sig2
+    lam = 0.1 * np.abs(ops.adjoint(p, d)).max()
+    m_star, hist_long = fista.solve(p, d, lam, 1500, gamma, history=True)
+    f_star = min(hist_long)
+    _, hist = fista.solve(p, d, lam, 60, gamma, history=True)
+    k = np.arange(1, 61)
+    bound = 2.0 * float(np.sum(m_star ** 2)) / (gamma * (k + 1) ** 2)
+    gap = np.array(hist) - f_star
+    assert np.all(gap <= bound * 1.001 + 1e-12 * abs(f_star))
+    # and the momentum is doing something: FISTA is ahead of ISTA at k = 60
+    _, hist_ista = fista.solve(p, d, lam, 60, gamma, momentum=False, history=True)
+    assert hist[-1] - f_star < hist_ista[-1] - f_star
 
 
 def _sparse_case(seed=14):
