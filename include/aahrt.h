@@ -409,15 +409,18 @@ int aahrt_plan_stage_times(aahrt_plan *plan, double *times_ms,
  * external memory manager, or loops that forbid allocation on their hot
  * path).  The paper has no counterpart: it concerns memory management only.
  * Scratch (spectra and a work counter) comes from one array of
- * AAHRT_NOALLOC_SCRATCH_BYTES that the library reserves in device memory at
- * load time on every GPU that loads it, held until the process exits; the
- * call allocates nothing.  m and d must be device memory.  Plans whose
- * spectra need more than the array (aahrt_plan_info xspec_len + yspec_len
- * complex values, plus 256 bytes) get AAHRT_ERR_UNSUPPORTED.  The first call
- * on a device looks up the array's address (cudaGetSymbolAddress) and caches
- * it: make that first call before any stream capture.  Every call shares the
- * array, which keeps the last call's contents; calls whose kernels overlap
- * on the GPU race on it and must be serialised. */
+ * AAHRT_NOALLOC_SCRATCH_BYTES in device memory, shared by all plans and held
+ * on every device it was committed on until the process exits; the call
+ * allocates nothing.  The array is committed, and its address looked up
+ * (cudaGetSymbolAddress), when a plan is created on a device
+ * (aahrt_plan_create / aahrt_plan_create_batched, which fail if that fails):
+ * the call itself loads nothing.  After a cudaDeviceReset, create a new plan
+ * before calling this again (old plans are invalid after a reset).  m and d
+ * must be device memory.  Plans whose spectra need more than the array
+ * (aahrt_plan_info xspec_len + yspec_len complex values, plus 256 bytes) get
+ * AAHRT_ERR_UNSUPPORTED.  Every call shares the array, which keeps the last
+ * call's contents; calls whose kernels overlap on the GPU race on it and
+ * must be serialised. */
 #define AAHRT_NOALLOC_SCRATCH_BYTES (16u << 20)
 int aahrt_forward_noalloc(aahrt_plan *plan, const float *m, float *d, void *stream);
 

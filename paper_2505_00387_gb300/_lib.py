@@ -26,6 +26,7 @@ AAHRT_SLICE_DIRECT = 2
 AAHRT_PRECISION_FP32 = 0
 AAHRT_PRECISION_SPLIT_BF16 = 1
 AAHRT_NSTAGES = 7
+AAHRT_NOALLOC_SCRATCH_BYTES = 16 << 20
 STAGE_NAMES = ("stretch_fft", "slice_fwd", "ifft_unstretch", "unstretchT_fft",
                "slice_adj", "ifft_stretchT", "solver_updates")
 

@@ -667,6 +667,13 @@ int aahrt_plan_create(aahrt_plan **out, const aahrt_geom *geom, const aahrt_opts
     Plan *p = nullptr;
     int rc = make_plan(&p, G, 1, geom, opts);
     if (rc) return rc;
+    {
+        DeviceGuard g(p->device);
+        if ((rc = noalloc_prepare(p->device))) {
+            free_plan(p);
+            return rc;
+        }
+    }
     *out = new aahrt_plan{p};
     return AAHRT_OK;
 }
@@ -681,6 +688,13 @@ int aahrt_plan_create_batched(aahrt_plan **out, int ncube, const aahrt_geom *geo
     Plan *p = nullptr;
     int rc = make_plan(&p, ncube, ncube, geoms, opts);
     if (rc) return rc;
+    {
+        DeviceGuard g(p->device);
+        if ((rc = noalloc_prepare(p->device))) {
+            free_plan(p);
+            return rc;
+        }
+    }
     *out = new aahrt_plan{p};
     return AAHRT_OK;
 }

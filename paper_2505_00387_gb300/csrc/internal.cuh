@@ -267,6 +267,10 @@ struct DeviceGuard {
     }
 };
 
+// Resolves and caches the allocation-free forward's scratch address on
+// device `dev` (current); called at plan creation (noalloc.cu).
+int noalloc_prepare(int dev);
+
 // operator application used by the C ABI and the solver
 int apply_forward(Plan &p, const float *m, float *d, cudaStream_t st,
                   int epi = EPI_STORE, const float *dobs = nullptr, bool blocked = false);

@@ -7,18 +7,23 @@
 // that forbid allocation and freeing on their hot path.  aahrt_forward
 // itself runs on the plan's workspace, but that workspace is one per plan;
 // this entry point instead takes its scratch (the model and data spectra and
-// the slice kernels' work counter) from one array of fixed size that the
-// library reserves in device memory when it is loaded, and allocates nothing.
+// the slice kernels' work counter) from one array of fixed size in device
+// memory, and allocates nothing.
 //
-// The array is a file-scope __device__ variable, so every GPU that loads the
-// library holds it until the process exits.  Host code cannot use its name as
-// a device address: the first call on each device looks the address up with
-// cudaGetSymbolAddress (with that device current) and caches it, so make that
-// first call before any stream capture.  All calls share the array and it
-// keeps the last call's contents; the work counter is cleared on every call
-// and the spectra are fully overwritten.  Calls whose kernels overlap on the
-// GPU (different streams without ordering, or several host threads) race on
-// the array: serialise them.
+// The array is a file-scope __device__ variable, so every GPU that holds it
+// keeps it until the process exits.  With lazy module loading the array is
+// committed when this file's module is first loaded on a device; plan
+// creation (aahrt_plan_create, aahrt_plan_create_batched) does that, with the
+// plan's device current, and looks the array's address up with
+// cudaGetSymbolAddress.  Host code cannot use the array's name as a device
+// address, so the address of each device is cached and every plan creation
+// refreshes it (after a cudaDeviceReset, old plans are invalid anyway and a
+// new plan brings a valid address).  The transform call itself therefore
+// neither loads a module nor commits memory, and can follow a stream capture.
+// All calls share the array and it keeps the last call's contents; the work
+// counter is cleared on every call and the spectra are fully overwritten.
+// Calls whose kernels overlap on the GPU (different streams without
+// ordering, or several host threads) race on the array: serialise them.
 #include <mutex>
 #include <vector>
 
@@ -31,16 +36,25 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[AAHRT_NOALLOC_S
 static std::mutex g_noalloc_mu;
 static std::vector<void *> g_noalloc_addr;   // per device ordinal
 
-// Device address of the array on device `dev`, which must be current.
-static int noalloc_base(int dev, unsigned char **out) {
+// Looks up the array's address on device `dev` (which must be current) and
+// caches it; loads this module there first if module loading is lazy.
+int noalloc_prepare(int dev) {
+    void *ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr) return cuda_fail(e, "allocation-free scratch array address");
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
     if ((int)g_noalloc_addr.size() <= dev) g_noalloc_addr.resize(dev + 1, nullptr);
-    if (!g_noalloc_addr[dev]) {
-        void *ptr = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess || !ptr) return cuda_fail(e, "scratch array address");
-        g_noalloc_addr[dev] = ptr;
-    }
+    g_noalloc_addr[dev] = ptr;
+    return AAHRT_OK;
+}
+
+// The cached address of device `dev`, set by plan creation on that device.
+static int noalloc_base(int dev, unsigned char **out) {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if ((int)g_noalloc_addr.size() <= dev || !g_noalloc_addr[dev])
+        return set_error(AAHRT_ERR_INVALID_ARG,
+                         "no allocation-free scratch address for device %d (plan not created "
+                         "through aahrt_plan_create)", dev);
     *out = static_cast<unsigned char *>(g_noalloc_addr[dev]);
     return AAHRT_OK;
 }
@@ -54,9 +68,10 @@ using namespace aahrt;
 extern "C" int aahrt_forward_noalloc(aahrt_plan *plan, const float *m, float *d, void *stream) {
     if (!plan) return set_error(AAHRT_ERR_INVALID_ARG, "plan is NULL");
     Plan &p = *plan->p;
-    int prev = -1;
-    cudaGetDevice(&prev);
-    if (prev != p.device) cudaSetDevice(p.device);
+    DeviceGuard g(p.device);
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess || cur != p.device)
+        return set_error(AAHRT_ERR_CUDA, "cannot make the plan's device %d current", p.device);
     int rc = AAHRT_OK;
     do {
         if ((rc = check_dev_ptr(m, "m")) || (rc = check_dev_ptr(d, "d"))) break;
@@ -90,6 +105,5 @@ extern "C" int aahrt_forward_noalloc(aahrt_plan *plan, const float *m, float *d,
             break;
         }
     } while (0);
-    if (prev >= 0 && prev != p.device) cudaSetDevice(prev);
     return rc;
 }

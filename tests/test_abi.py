@@ -44,6 +44,22 @@ def test_library_exports_every_declared_symbol(lib):
     assert set(declared_functions()) == set(L._SIGS)
 
 
+def test_binding_constants_match_header():
+    """Every AAHRT_* integer the binding defines equals the header's #define
+    or enumerator of the same name."""
+    txt = re.sub(r"/\*.*?\*/", "", "".join(open(h).read() for h in HEADERS), flags=re.S)
+    vals = {}
+    for m in re.finditer(r"^#define\s+(AAHRT_\w+)\s+(\S[^\n]*?)\s*$", txt, re.M):
+        expr = re.sub(r"(\d+)u\b", r"\1", m.group(2))
+        if re.fullmatch(r"[-\d<>() ]+", expr):
+            vals[m.group(1)] = int(eval(expr, {}, {}))
+    names = [n for n in dir(L) if n.startswith("AAHRT_") and isinstance(getattr(L, n), int)]
+    assert "AAHRT_NOALLOC_SCRATCH_BYTES" in names
+    for n in names:
+        assert n in vals, n
+        assert getattr(L, n) == vals[n], n
+
+
 def test_status_strings(lib):
     assert L.aahrt_status_string(0) == "success"
     assert L.aahrt_status_string(-1) == "invalid argument"
