@@ -35,3 +35,20 @@ def oracle_H(p, X):
     Xd = X.copy()
     Xd[1:] *= 2.0
     return ops.rfft_bins_T(p, Xd)
+
+
+def dot_rel_conditioned(gp, oracle_fwd, seed):
+    """FP32 dot test of the GPU pair on a well-conditioned pair of vectors:
+    m random and d = L m (by the oracle, `oracle_fwd` maps the flat model to
+    the flat data) plus as much independent noise, so <L m, d> is about
+    |L m|^2.  For two independent random vectors <L m, d> is itself a random
+    projection, often near zero, and the relative error of the test would
+    measure that cancellation rather than the adjointness."""
+    rng = np.random.default_rng(seed)
+    m = rng.standard_normal(gp.model_len).astype(np.float32).astype(np.float64)
+    lm = np.asarray(oracle_fwd(m), np.float64).ravel()
+    d = lm + np.sqrt(np.mean(lm * lm)) * rng.standard_normal(lm.shape)
+    d = d.astype(np.float32).astype(np.float64)
+    lhs = float(np.dot(host(gp.forward(dev(m))), d))
+    rhs = float(np.dot(host(gp.adjoint(dev(d))), m))
+    return abs(lhs - rhs) / abs(lhs)

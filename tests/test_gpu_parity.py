@@ -11,7 +11,7 @@ import oracle
 from oracle import fista, ops
 from paper_2505_00387_gb300 import synthetic as syn
 
-from gpu_util import dev, gpu_plan, host, oracle_H, oracle_plan, rel
+from gpu_util import dev, dot_rel_conditioned, gpu_plan, host, oracle_H, oracle_plan, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -87,21 +87,16 @@ def test_forward_adjoint_small_cube(small_case):
     assert rel(m, ops.adjoint(p, dr)) < TOL_OP
 
 
-def _dot_test(gp, seed):
-    rng = np.random.default_rng(seed)
-    m = rng.standard_normal(gp.model_len)
-    d = rng.standard_normal(gp.data_len)
-    Lm = host(gp.forward(dev(m)))
-    Ltd = host(gp.adjoint(dev(d)))
-    m32 = m.astype(np.float32).astype(np.float64)
-    d32 = d.astype(np.float32).astype(np.float64)
-    a = float(np.dot(Lm, d32))
-    b = float(np.dot(m32, Ltd))
-    return abs(a - b) / abs(a)
+def _dot_test(gp, p, seed):
+    """Relative FP32 dot-test error on a well-conditioned pair (d = L m by
+    the oracle plan p, plus noise)."""
+    return dot_rel_conditioned(
+        gp, lambda m: ops.forward(p, m.reshape(p.ntau, p.nq, p.ntheta)), seed)
 
 
 def test_dot_product_small_cube(small_case):
-    assert _dot_test(small_case[2], 22) < TOL_DOT
+    g, p, gp = small_case
+    assert _dot_test(gp, p, 22) < TOL_DOT
 
 
 def test_fista_small_cube(small_case):
@@ -156,7 +151,7 @@ def test_ragged_multigroup(interp, tg, w):
     tol = TOL_OP if w >= 6 else 5e-4
     assert rel(host(gp.forward(dev(m)), (g.nt, g.ntr)), ops.forward(p, m)) < tol
     assert rel(host(gp.adjoint(dev(d)), m.shape), ops.adjoint(p, d)) < tol
-    assert _dot_test(gp, 32) < TOL_DOT
+    assert _dot_test(gp, p, 32) < TOL_DOT
 
 
 @pytest.mark.parametrize("case", ["one_azimuth", "one_curvature", "zero_offset",
@@ -192,11 +187,7 @@ def test_edge_cases(case):
     d = rng.standard_normal((g.nt, g.ntr))
     assert rel(host(gp.forward(dev(m)), (g.nt, g.ntr)), ops.forward(p, m)) < TOL_OP
     assert rel(host(gp.adjoint(dev(d)), m.shape), ops.adjoint(p, d)) < TOL_OP
-    # These cases are tiny (a few thousand samples) with <Lm, d> 300-800 times
-    # below |Lm||d|, so FP32 rounding of the two paths shows up ~10x larger in
-    # the relative dot test than at the configurations' sizes; the bound for
-    # them is 1e-5 (every configuration-sized case keeps 1e-6).
-    assert _dot_test(gp, 41) < 1e-5
+    assert _dot_test(gp, p, 41) < TOL_DOT
 
 
 def test_plan_refuses_oversized_frame():
@@ -231,7 +222,17 @@ def test_batched_cubes_match_oracle():
         assert rel(mg[off_m:off_m + n_m].reshape(m.shape), ops.adjoint(p, d)) < TOL_OP
         off_d += n_d
         off_m += n_m
-    assert _dot_test(gp, 51) < TOL_DOT
+    plans = [oracle.make_plan(**c.geom_kwargs(), r2max=r2max) for c in cubes]
+
+    def fwd_all(mflat):
+        out, off = [], 0
+        for c, pc in zip(cubes, plans):
+            n = c.ntau * c.nq * c.ntheta
+            out.append(ops.forward(pc, mflat[off:off + n].reshape(c.ntau, c.nq, c.ntheta)).ravel())
+            off += n
+        return np.concatenate(out)
+
+    assert dot_rel_conditioned(gp, fwd_all, 51) < TOL_DOT
 
 
 def test_shared_geometry_gathers_match_single():
@@ -306,7 +307,8 @@ def test_paper_gather_sampled_forward_adjoint(paper_case):
 
 
 def test_paper_gather_dot_product(paper_case):
-    assert _dot_test(paper_case[2], 71) < TOL_DOT
+    g, p, gp = paper_case
+    assert _dot_test(gp, p, 71) < TOL_DOT
 
 
 def test_paper_gather_fista_few_iterations(paper_case):
@@ -317,3 +319,21 @@ def test_paper_gather_fista_few_iterations(paper_case):
     mo = fista.solve(p, d, lam, 3, gamma)
     mg, _ = gp.sparse_solve(dev(d), lam, 3, gamma=gamma)
     assert rel(host(mg, mo.shape), mo) < TOL_FISTA
+
+
+@pytest.mark.slow
+def test_paper_gather_fista_100_iterations(paper_case):
+    """The paper-scale gather's full solve: 100 FISTA iterations through
+    aahrt_sparse_solve against the oracle's solve with the oracle's step
+    (0.95 / sigma^2 from 30 power iterations) and threshold
+    (lambda = 0.05 max|L^T d|), on the whole model cube."""
+    g, p, gp = paper_case
+    d = g.d
+    lam = 0.05 * float(np.abs(ops.adjoint(p, d)).max())
+    gamma = 0.95 / fista.power_sigma2(p, d, iters=30)
+    mo = fista.solve(p, d, lam, 100, gamma)
+    for graph in (True, False):
+        mg, info = gp.sparse_solve(dev(d), lam, 100, gamma=gamma, use_graph=graph)
+        assert info.iters == 100
+        err = rel(host(mg, mo.shape), mo)
+        assert err < TOL_FISTA, f"graph={graph}: rel {err:.3e}"
