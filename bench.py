@@ -1,28 +1,32 @@
 #!/usr/bin/env python3
 """Throughput of the AAHRT operator pair inside the FISTA sparse solve.
 
-One step = one sparse solve (100 FISTA iterations; each iteration is one
+Default workload (the batched form): 512 CMP cubes (nt = 1001 at 4 ms, fold
+200-3000 in 90-360 degree sectors of a 3 km disc, 64 curvatures x 24
+azimuths) in one autotuned plan; one step = one 50-iteration FISTA solve of
+every cube, each with its own step and threshold (each iteration is one
 forward + adjoint pair with the residual and the shrinkage/momentum update
-fused) of the paper-scale gather: nt = 1001 at 4 ms, 2000 traces uniform in
-a 3 km disc, 100 curvatures x 36 azimuths, 30 Ricker events + 10% noise
-(synthetic, seeded).  value = pairs/s over the whole job; gathers/s is the
-same rate per 100-iteration solve.  Inputs are resident in HBM for `value`;
-`e2e` passes pinned host buffers to the C ABI so the host<->device copies
-of d and m are inside the timed region.  L2 is flushed (256 MB write)
-between timed steps.
+fused).  value = cube-pairs/s over the whole job; gathers/s is the rate of
+whole cube solves.  Inputs are resident in HBM for `value` (26 GB of spectra,
+far beyond L2, and L2 is flushed between timed steps); `e2e` passes pinned
+host buffers to the C ABI so the host<->device copies of d and m are inside
+the timed region.  The same JSON line carries, under "gather", the line of
+the paper-scale single gather (nt = 1001, 2000 traces in a 3 km disc, 100
+curvatures x 36 azimuths; one step = one 100-iteration FISTA solve).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--workload gather|batch512|slowness|table1|shared64]
+                  [--workload batch512|gather|slowness|table1|shared64]
 
---workload batch512 times the batched form instead: 512 CMP cubes (nt = 1001,
-fold 200-3000, offsets in a 3 km disc over a random 90-360 degree azimuth
-sector, 64 curvatures x 24 azimuths) in one autotuned plan, one step = one
-50-iteration FISTA solve of every cube with its own step and threshold.
+--workload gather times the single gather alone.
 
 --workload slowness times the same gather and solve on a uniform slowness
 axis (100 slownesses 1/3500..1/1500 s/m, so the curvatures q = p^2 are not
 uniform): the slice step is the direct sum of the DFT along q (a type-3
 DFT), whose roofline is the special-function rate of the phases.
+
+--workload shared64 times 64 gathers sharing one 8000-trace geometry: the
+split-BF16 tensor-core plan of all 64, the FP32 plan of all 64, and one
+single-gather FP32 plan applied to the 64 gathers in turn.
 
 Under torchrun each rank runs an independent replica on its own GPU (the
 path needs no communication); rank 0 prints one JSON line.
@@ -51,6 +55,8 @@ BATCH_ITERS = 50
 BATCH_WORKLOAD = ("512 CMP cubes: nt=1001 dt=4ms, fold 200-3000 in 90-360 degree sectors "
                   "of a 3 km disc, 64 q x 24 azimuths, one autotuned plan; one step = one "
                   "50-iteration FISTA solve of every cube (per-cube step and threshold)")
+L2_NOTE = "inputs far larger than L2 (spectra of tens of GB), and L2 flushed (256 MB write)"
+L2_NOTE_GATHER = "L2 flushed between timed steps (256 MB write)"
 
 
 def parse():
@@ -60,8 +66,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="gather",
+    ap.add_argument("--workload", default="batch512",
                     choices=["gather", "batch512", "slowness", "table1", "shared64"])
+    ap.add_argument("--oracle-single-core", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -188,10 +195,10 @@ def launch_bytes(info, launches, iters_total):
 
 
 def traffic_record(stage):
-    """DRAM bytes per launch of a stage's kernel from the committed ncu
-    summary, if the files that define that kernel (its source, the headers it
-    includes and the plan code that sizes its launch) still hash to the ones
-    the counters were taken on."""
+    """The committed ncu record of a stage's kernel (DRAM bytes per launch
+    and, where taken, issue and FMA-pipe fractions), if the files that define
+    that kernel (its source, the headers it includes and the plan code that
+    sizes its launch) still hash to the ones the counters were taken on."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
@@ -205,14 +212,52 @@ def traffic_record(stage):
             h.update(open(os.path.join(ROOT, f), "rb").read())
         if rec.get("sha256") != h.hexdigest():
             return None
-        return rec.get("dram_bytes")
+        return rec
     except Exception:
         return None
 
 
+# ------------------------------------------------------------- workloads
+def batch_geometry(seed):
+    """The 512 cubes' geometry (no data) and the batch-wide largest squared
+    offset that fixes their shared stretched-time plan."""
+    import numpy as np
+    from paper_2505_00387_gb300 import synthetic as syn
+    geo = syn.cube_batch(seed=seed, with_data=False)
+    r2max = max(float(np.max(c.hx ** 2 + c.hy ** 2)) for c in geo)
+    return geo, r2max
+
+
+def fold_picks(folds, n):
+    """n cubes spread evenly over the fold range (quantiles of the sorted
+    folds)."""
+    import numpy as np
+    order = np.argsort(np.asarray(folds), kind="stable")
+    return [int(order[int(round(q * (len(folds) - 1)))]) for q in np.linspace(0.0, 1.0, n)]
+
+
+def workload_config(kind, world=1, geo=None, g=None):
+    """The config object of a bench line: the workload only (sizes, iteration
+    count, L2 treatment), the same for the GPU arm and the reference arm."""
+    if kind == "batch512":
+        folds = [c.ntr for c in geo]
+        c0 = geo[0]
+        return {"workload": BATCH_WORKLOAD, "ncube": len(geo), "nt": c0.nt, "dt": c0.dt,
+                "fold_min": min(folds), "fold_max": max(folds),
+                "traces_total": int(sum(folds)), "nq": c0.nq, "ntheta": c0.ntheta,
+                "fista_iters_per_step": BATCH_ITERS, "l2": L2_NOTE,
+                "parallelism": f"replicas x{world}"}
+    cfg = {"workload": SLOW_WORKLOAD if kind == "slowness" else WORKLOAD, "nt": g.nt,
+           "dt": g.dt, "ntr": g.ntr, "nq": g.nq, "ntheta": g.ntheta,
+           "fista_iters_per_step": ITERS, "l2": L2_NOTE_GATHER,
+           "parallelism": f"replicas x{world}"}
+    if kind == "slowness":
+        cfg["slice_step"] = "direct sum (type-3 DFT along q)"
+    return cfg
+
+
 # ------------------------------------------------------------------ ours
 def run_ours(args):
-    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -227,13 +272,31 @@ def run_ours(args):
         B.build()
     if world > 1:
         dist.barrier()
+    line = measure(args.workload, args, rank, world, dev)
+    if args.workload == "batch512":
+        # the paper-scale single gather, measured the same way in the same run
+        line["gather"] = measure("gather", args, rank, world, dev)
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def measure(kind, args, rank, world, dev):
+    """One bench line of workload `kind` (batch512, gather or slowness) on
+    this rank's GPU; only rank 0's return value is complete."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
     from paper_2505_00387_gb300 import _lib as L
     from paper_2505_00387_gb300 import synthetic as syn
     from paper_2505_00387_gb300.plan import AahrtPlan
 
-    batch = args.workload == "batch512"
-    slow = args.workload == "slowness"
+    batch = kind == "batch512"
+    slow = kind == "slowness"
     qa = None
+    g = cubes = None
     if batch:
         cubes = syn.cube_batch(seed=replica_seed(3, rank))
         gp = AahrtPlan.batched(cubes, autotune=True)
@@ -274,7 +337,9 @@ def run_ours(args):
         step()
     torch.cuda.synchronize()
 
-    def timed(fn, k, profile=False):
+    per_step = []
+
+    def timed(fn, k):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(k)]
         if world > 1:
@@ -292,10 +357,8 @@ def run_ours(args):
         per_step.extend(a.elapsed_time(b) for a, b in ev)
         return sum(per_step)
 
-    per_step = []
-
     t_launch0 = gp.stage_times()[1]
-    sampler = ClockSampler(local)
+    sampler = ClockSampler(local_index(dev))
     sampler.start()
     total_ms = timed(step, args.steps)
     step_median_ms = statistics.median(per_step)
@@ -322,55 +385,34 @@ def run_ours(args):
 
     step_e2e()
     torch.cuda.synchronize()
-    e2e_ms = timed(step_e2e, args.steps)
-    e2e_value, _ = job_rate(e2e_ms, args.steps * pairs_per_step, world, dev)
+    e2e_steps = args.steps if not batch else min(args.steps, 5)
+    e2e_ms = timed(step_e2e, e2e_steps)
+    e2e_value, _ = job_rate(e2e_ms, e2e_steps * pairs_per_step, world, dev)
 
     # per-stage device time over the same kind of steps (eager launches,
     # CUDA events around every stage on the launching stream)
     gp.set_profiling(True)
-    for _ in range(args.steps):
+    for _ in range(args.steps if not batch else min(args.steps, 2)):
         flush.zero_()
         gp.sparse_solve(d, lam, iters, m, use_graph=False, want_info=False, **kw)
     torch.cuda.synchronize()
     st_ms, st_n = gp.stage_times()
     gp.set_profiling(False)
 
-    if world > 1:
-        dist.destroy_process_group()
     if rank != 0:
-        return
-
+        return None
+    config = workload_config(kind, world, geo=cubes, g=g)
+    plan_desc = {"nfft": info.nfft, "nbins": info.nbins, "spread_width": info.spread_width,
+                 "theta_group": info.theta_group, "time_pairs": info.time_pairs}
     if batch:
-        folds = [c.ntr for c in cubes]
-        config = {"workload": BATCH_WORKLOAD, "ncube": len(cubes), "nt": cubes[0].nt,
-                  "dt": cubes[0].dt, "fold_min": min(folds), "fold_max": max(folds),
-                  "traces_total": int(sum(folds)), "nq": cubes[0].nq,
-                  "ntheta": cubes[0].ntheta, "fista_iters_per_step": iters,
-                  "nfft": info.nfft, "nbins": info.nbins,
-                  "autotuned": {"spread_width": info.spread_width,
-                                "theta_group": info.theta_group,
-                                "time_pairs": info.time_pairs},
-                  "l2": "inputs (%.1f GB spectra) far larger than L2, and flushed" %
-                        ((info.xspec_len + info.yspec_len) * 8 / 1e9),
-                  "parallelism": f"replicas x{world}"}
-    else:
-        config = {"workload": SLOW_WORKLOAD if slow else WORKLOAD, "nt": g.nt, "dt": g.dt,
-                  "ntr": g.ntr, "nq": g.nq, "ntheta": g.ntheta, "fista_iters_per_step": iters,
-                  "nfft": info.nfft, "nbins": info.nbins,
-                  "l2": "flushed between timed steps (256 MB write)",
-                  "parallelism": f"replicas x{world}"}
-        if slow:
-            config["slice_step"] = "direct sum (type-3 DFT along q)"
-            config["theta_group"] = info.theta_group
-        else:
-            config["spread_width"] = info.spread_width
+        plan_desc["autotuned"] = True
     sb = launch_bytes(info, st_n, args.steps * iters)
     names = L.STAGE_NAMES
     per_launch = [st_ms[i] / st_n[i] if st_n[i] else 0.0 for i in range(L.AAHRT_NSTAGES)]
     top = max(range(6), key=lambda i: st_ms[i])
     peak, peak_kind = peaks()
     achieved = sb[top] / (per_launch[top] * 1e-3) / 1e9
-    iter_ms = sum(st_ms[:6]) / (args.steps * iters)
+    iter_ms = sum(st_ms[:6]) / sum(st_n[1:2] or [1])
     iter_bytes = sum(stage_bytes(info)[:6])
     fused = st_n[3] == 0 and st_n[2] > 0
     kernel_names = ["r2c_kernel", "slice_fwd_kernel",
@@ -378,7 +420,8 @@ def run_ours(args):
                     "slice_adj_kernel", "c2r_r2c_kernel" if fused else "c2r_kernel"]
     if slow:
         kernel_names[1], kernel_names[4] = "direct_fwd_kernel", "direct_adj_kernel"
-    tr = None if batch else traffic_record(names[top] + ("@direct" if slow else ""))
+    suffix = "@direct" if slow else ("@batch512" if batch else "")
+    rec = traffic_record(names[top] + suffix)
     line = {
         "metric": METRIC,
         "value": round(value, 3),
@@ -394,13 +437,16 @@ def run_ours(args):
         "dtype": "f32",
         "data": "synthetic",
         "config": config,
+        "plan": plan_desc,
         "gathers_per_s": round(value / iters, 4),
         "e2e": {"value": round(e2e_value, 3), "unit": "pairs/s",
-                "h2d_bytes_per_step": 4 * gp.data_len, "d2h_bytes_per_step": 4 * gp.model_len},
+                "h2d_bytes_per_step": 4 * gp.data_len, "d2h_bytes_per_step": 4 * gp.model_len,
+                "steps": e2e_steps},
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": tr, "kernel": kernel_names[top], "stage": names[top],
+                     "traffic": rec.get("dram_bytes") if rec else None,
+                     "kernel": kernel_names[top], "stage": names[top],
                      "bytes_per_launch": sb[top],
                      "avg_launch_ms": round(per_launch[top], 5),
                      "peak_source": peak_kind},
@@ -418,6 +464,18 @@ def run_ours(args):
                    for i in range(L.AAHRT_NSTAGES) if st_n[i]},
         "clocks": clocks,
     }
+    if not slow:
+        # the slice steps' own bound: issue slots and the FP32 pipe (ncu, one
+        # launch of each kernel on the same workload shape, while the sources
+        # still hash to the captured ones)
+        alu = {}
+        for st in ("slice_fwd", "slice_adj"):
+            r = traffic_record(st + suffix)
+            if r and "issue_active" in r:
+                alu[st] = {"issue_active": r["issue_active"], "fma_pipe": r.get("fma_pipe"),
+                           "kernel": r["kernel"]}
+        if alu:
+            line["slice_issue"] = alu
     if slow and top in (1, 4):
         # the direct sum is bound by the phases' sine/cosine pairs: one per
         # (bin, trace, curvature) and launch; peak = SMs x 16 special-function
@@ -429,7 +487,8 @@ def run_ours(args):
         ach = phases / (per_launch[top] * 1e-3) / 1e9
         line["roofline"] = {"bound": "alu", "achieved": round(ach, 1),
                             "peak": round(peak_ph, 1), "unit": "Gphase/s",
-                            "frac": round(ach / peak_ph, 4), "traffic": tr,
+                            "frac": round(ach / peak_ph, 4),
+                            "traffic": rec.get("dram_bytes") if rec else None,
                             "kernel": kernel_names[top], "stage": names[top],
                             "phases_per_launch": phases,
                             "bytes_per_launch": sb[top],
@@ -439,17 +498,63 @@ def run_ours(args):
     if world == 1 and not args.no_cpu_baseline:
         if batch:
             line["cpu_baseline"], line["err_vs_fp64"] = cpu_baseline_batch(cubes, gp, d, dev)
+            line["err_vs_fp64"]["fista"] = fista_error_batch(cubes, gp, d, dev, cg, cl)
         else:
-            line["cpu_baseline"], line["err_vs_fp64"] = cpu_baseline(g, gp, d, dev, q_axis=qa)
-    print(json.dumps(line), flush=True)
+            line["cpu_baseline"], line["err_vs_fp64"] = cpu_baseline(g, gp, d, dev, q_axis=qa,
+                                                                     kind=kind)
+    return line
 
 
-def cpu_baseline(g, gp, d_dev, dev, pairs=6, q_axis=None):
+def local_index(dev):
+    return dev.index if dev.index is not None else 0
+
+
+def single_core_seconds(kind, cube=None):
+    """Seconds of one FP64 forward+adjoint pair on one host core (a child
+    process with one OpenMP thread), or None if it fails."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-single-core",
+           kind if cube is None else f"{kind}:{cube}"]
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
+               MKL_NUM_THREADS="1")
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=600)
+        return float(json.loads(r.stdout.strip().splitlines()[-1])["seconds"])
+    except Exception:
+        return None
+
+
+def run_single_core(spec):
+    """Child of single_core_seconds: time one oracle pair of the gather or of
+    one cube of the batch (`batch512:<cube>`) and print the seconds."""
+    import numpy as np
+
+    import oracle
+    from oracle import ops
+    from paper_2505_00387_gb300 import synthetic as syn
+    kind, _, cube = spec.partition(":")
+    if kind == "batch512":
+        geo, r2max = batch_geometry(3)
+        c = syn.cube_batch(seed=3, cubes=[int(cube)])[0]
+        p = oracle.make_plan(**c.geom_kwargs(), r2max=r2max)
+        d = c.d
+    else:
+        c = syn.paper_gather(seed=1)
+        p = oracle.make_plan(**c.geom_kwargs())
+        d = c.d
+    mr = np.random.default_rng(5).standard_normal((c.ntau, c.nq, c.ntheta))
+    ops.slice_forward(p.subset_traces([0]), np.zeros((p.nbins, p.nq, p.ntheta), complex))
+    t0 = time.perf_counter()
+    ops.forward(p, mr)
+    ops.adjoint(p, d)
+    el = time.perf_counter() - t0
+    print(json.dumps({"seconds": el, "threads": ops.threads()}))
+
+
+def cpu_baseline(g, gp, d_dev, dev, pairs=6, q_axis=None, kind="gather"):
     """The FP64 checker timed on this host's cores on a bounded sample of the
     same workload (`pairs` forward+adjoint pairs of the full gather), and
     the GPU path's relative error against those FP64 results."""
     import numpy as np
-    import torch
 
     import oracle
     from oracle import ops
@@ -463,12 +568,14 @@ def cpu_baseline(g, gp, d_dev, dev, pairs=6, q_axis=None):
         d_or = ops.forward(p, mr)
         m_or = ops.adjoint(p, g.d)
     el = time.perf_counter() - t0
-    d_gpu = gp.forward(torch.from_numpy(mr.astype(np.float32).ravel()).to(dev))
+    d_gpu = gp.forward(torch_from(mr, dev))
     m_gpu = gp.adjoint(d_dev)
     d_gpu = d_gpu.cpu().numpy().astype(np.float64).reshape(d_or.shape)
     m_gpu = m_gpu.cpu().numpy().astype(np.float64).reshape(m_or.shape)
     err = {"forward_rel_l2": float(np.linalg.norm(d_gpu - d_or) / np.linalg.norm(d_or)),
-           "adjoint_rel_l2": float(np.linalg.norm(m_gpu - m_or) / np.linalg.norm(m_or))}
+           "adjoint_rel_l2": float(np.linalg.norm(m_gpu - m_or) / np.linalg.norm(m_or)),
+           "fista": "not run here (a 100-iteration FP64 solve takes minutes); "
+                    "tests/test_gpu_parity.py::test_paper_gather_fista_100_iterations"}
     cb = {"value": round(pairs / el, 5), "unit": "pairs/s", "cores": ops.threads(),
           "kind": "oracle",
           "sample": f"{pairs} forward+adjoint pairs of the full gather, FP64, "
@@ -476,10 +583,17 @@ def cpu_baseline(g, gp, d_dev, dev, pairs=6, q_axis=None):
     return cb, err
 
 
+def torch_from(a, dev):
+    import numpy as np
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32).ravel()).to(dev)
+
+
 def cpu_baseline_batch(cubes, gp, d_dev, dev, nsample=8):
     """The FP64 checker on one forward+adjoint pair of each of nsample cubes
-    spread over the fold range (on the batch's shared time plan), extrapolated
-    per cube pair, and the GPU error on those cubes."""
+    spread over the fold range (on the batch's shared time plan), as cube
+    pairs per second on all host cores and on one core, and the GPU error on
+    those cubes."""
     import numpy as np
     import torch
 
@@ -487,8 +601,7 @@ def cpu_baseline_batch(cubes, gp, d_dev, dev, nsample=8):
     from oracle import ops
 
     folds = np.array([c.ntr for c in cubes])
-    order = np.argsort(folds, kind="stable")
-    picks = [int(order[int(round(q * (len(cubes) - 1)))]) for q in np.linspace(0.0, 1.0, nsample)]
+    picks = fold_picks(folds, nsample)
     r2max = max(float(np.max(x.hx ** 2 + x.hy ** 2)) for x in cubes)
     rng = np.random.default_rng(124)
     m_all = rng.standard_normal(gp.model_len).astype(np.float32)
@@ -514,19 +627,58 @@ def cpu_baseline_batch(cubes, gp, d_dev, dev, nsample=8):
            "forward_rel_l2_max": max(ef), "adjoint_rel_l2_max": max(ea),
            "forward_rel_l2_median": float(np.median(ef)),
            "adjoint_rel_l2_median": float(np.median(ea))}
+    mid = picks[len(picks) // 2]
+    s1 = single_core_seconds("batch512", mid)
     cb = {"value": round(len(picks) / el, 5), "unit": "pairs/s", "cores": ops.threads(),
           "kind": "oracle",
           "sample": f"1 forward+adjoint pair of each of {len(picks)} cubes spread over the fold "
                     f"range ({int(folds[picks[0]])}-{int(folds[picks[-1]])} traces), FP64, "
-                    f"{el:.1f} s wall; pairs/s per cube pair"}
+                    f"{el:.1f} s wall; pairs/s per cube pair",
+          "single_core": ({"value": round(1.0 / s1, 5), "unit": "pairs/s", "cores": 1,
+                           "sample": f"1 pair of the median-fold cube of the sample "
+                                     f"({int(folds[mid])} traces), one OpenMP thread"}
+                          if s1 else None)}
     return cb, err
+
+
+def fista_error_batch(cubes, gp, d_dev, dev, cg, cl):
+    """Relative L2 error of the GPU's 50-iteration FISTA output against the
+    FP64 checker's on the smallest-fold cube of the batch: the checker
+    estimates that cube's step (30 power iterations) and threshold itself;
+    the GPU solves the whole batch with those two values for that cube."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from oracle import fista, ops
+
+    folds = np.array([c.ntr for c in cubes])
+    i = int(np.argmin(folds))
+    c = cubes[i]
+    r2max = max(float(np.max(x.hx ** 2 + x.hy ** 2)) for x in cubes)
+    p = oracle.make_plan(**c.geom_kwargs(), r2max=r2max)
+    t0 = time.perf_counter()
+    lam = 0.05 * float(np.abs(ops.adjoint(p, c.d)).max())
+    gamma = 0.95 / fista.power_sigma2(p, c.d, iters=30)
+    mo = fista.solve(p, c.d, lam, BATCH_ITERS, gamma)
+    el = time.perf_counter() - t0
+    g2, l2 = cg.copy(), cl.copy()
+    g2[i], l2[i] = gamma, lam
+    m = torch.zeros(gp.model_len, device=dev)
+    gp.sparse_solve(d_dev, 0.0, BATCH_ITERS, m, use_graph=False, want_info=False,
+                    per_cube=True, cube_gamma=g2, cube_lambda=l2)
+    msz = c.ntau * c.nq * c.ntheta
+    mg = m[i * msz:(i + 1) * msz].cpu().numpy().astype(np.float64).reshape(mo.shape)
+    return {"cube": i, "fold": int(folds[i]), "iters": BATCH_ITERS,
+            "rel_l2": float(np.linalg.norm(mg - mo) / np.linalg.norm(mo)),
+            "oracle_seconds": round(el, 1)}
 
 
 # ------------------------------------------------------------- reference
 def run_reference(args):
-    """The FP64 checker on the host cores, on the same workload and metric:
-    each step is a bounded sample (a fraction of the frequency bins of one
-    forward+adjoint pair), counted as that fraction of a pair."""
+    """The FP64 checker on the host cores, on the same workload, config and
+    metric: each step is a whole forward+adjoint pair (of one cube of the
+    batch, cubes taken over the fold range, or of the gather)."""
     rank, world, local = dist_info()
     if rank != 0:
         return
@@ -536,38 +688,50 @@ def run_reference(args):
     from oracle import ops
     from paper_2505_00387_gb300 import synthetic as syn
 
-    g = syn.paper_gather(seed=1)
-    p = oracle.make_plan(**g.geom_kwargs())
-    nsteps = args.steps + max(args.warmup, 3)
-    frac = min(1.0, 12.0 / nsteps)
-    nb = max(1, int(round(p.nbins * frac)))
-    frac = nb / p.nbins
+    kind = args.workload if args.workload in ("batch512", "gather", "slowness") else "batch512"
     rng = np.random.default_rng(123)
-    m = rng.standard_normal((g.ntau, g.nq, g.ntheta))
-    ps = p
+    if kind == "batch512":
+        geo, r2max = batch_geometry(3)
+        # timed steps: cubes evenly over the fold range; warm-up: a few more
+        timed_ = fold_picks([c.ntr for c in geo], args.steps)
+        warm = fold_picks([c.ntr for c in geo], max(args.warmup, 3))
+        need = sorted(set(timed_) | set(warm))
+        data = {c: x for c, x in zip(need, syn.cube_batch(seed=3, cubes=need))}
+        plans = {c: oracle.make_plan(**data[c].geom_kwargs(), r2max=r2max) for c in need}
 
-    def step():
-        X = ops.rfft_bins(ps, ops.stretch(ps, m.reshape(ps.ntau, -1))).reshape(
-            ps.nbins, ps.nq, ps.ntheta)
-        from dataclasses import replace
-        sub = replace(ps, kmax=nb - 1)
-        Y = ops.slice_forward(sub, np.ascontiguousarray(X[:nb]))
-        full = np.zeros((ps.nbins, ps.ntr), complex)
-        full[:nb] = Y
-        dd = ops.unstretch(ps, ops.irfft_bins(ps, full))
-        R = ops.irfft_bins_T(ps, ops.unstretch_T(ps, dd))
-        Xa = ops.slice_adjoint(sub, np.ascontiguousarray(R[:nb]))
-        fullx = np.zeros((ps.nbins, ps.nq * ps.ntheta), complex)
-        fullx[:nb] = Xa.reshape(nb, -1)
-        ops.stretch_T(ps, ops.rfft_bins_T(ps, fullx))
+        def step(c):
+            x = data[c]
+            mr = rng.standard_normal((x.ntau, x.nq, x.ntheta))
+            ops.forward(plans[c], mr)
+            ops.adjoint(plans[c], x.d)
+        seq_warm, seq = warm, timed_
+        config = workload_config("batch512", 1, geo=geo)
+        sample = (f"per step one forward+adjoint pair of one cube; the {args.steps} timed "
+                  f"steps take {args.steps} cubes evenly over the fold range "
+                  f"({geo[timed_[0]].ntr}-{geo[timed_[-1]].ntr} traces); FP64")
+    else:
+        g = syn.paper_gather(seed=1)
+        qa = None
+        if kind == "slowness":
+            from oracle import pnmo
+            qa = pnmo.q_axis_slowness(syn.P_MIN, syn.P_MAX, g.nq)
+        p = oracle.make_plan(**g.geom_kwargs(), q_axis=qa)
 
-    for _ in range(max(args.warmup, 3)):
-        step()
+        def step(_):
+            mr = rng.standard_normal((g.ntau, g.nq, g.ntheta))
+            ops.forward(p, mr)
+            ops.adjoint(p, g.d)
+        seq_warm, seq = [0] * max(args.warmup, 3), [0] * args.steps
+        config = workload_config(kind, 1, g=g)
+        sample = "per step one forward+adjoint pair of the full gather, FP64"
+
+    for c in seq_warm:
+        step(c)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
+    for c in seq:
+        step(c)
     el = time.perf_counter() - t0
-    value = args.steps * frac / el
+    value = len(seq) / el
     line = {
         "impl": "reference",
         "metric": METRIC,
@@ -582,13 +746,9 @@ def run_reference(args):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nt": g.nt, "dt": g.dt, "ntr": g.ntr, "nq": g.nq,
-                   "ntheta": g.ntheta, "fista_iters_per_step": ITERS, "nfft": p.nfft,
-                   "nbins": p.nbins, "parallelism": "host cores"},
+        "config": config,
         "cpu_baseline": {"value": round(value, 6), "unit": "pairs/s", "cores": ops.threads(),
-                         "kind": "oracle",
-                         "sample": f"per step {nb} of {p.nbins} frequency bins of one "
-                                   f"forward+adjoint pair (= {frac:.3f} pair), FP64"},
+                         "kind": "oracle", "sample": sample},
         "e2e": {"value": round(value, 6), "unit": "pairs/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -776,7 +936,9 @@ def run_shared64(args):
 
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "reference":
+    if a.oracle_single_core:
+        run_single_core(a.oracle_single_core)
+    elif a.impl == "reference":
         run_reference(a)
     elif a.workload == "table1":
         run_table1(a)

@@ -190,11 +190,13 @@ def paper_gather(seed: int = 1, ntr: int = 2000) -> Gather:
                   info=dict(name="cmp-1001t-2000tr-100q-36az", events=ev))
 
 
-def cube_batch(seed: int = 3, ncube: int = 512, cubes: Optional[List[int]] = None):
+def cube_batch(seed: int = 3, ncube: int = 512, cubes: Optional[List[int]] = None,
+               with_data: bool = True):
     """Batch of CMP cubes: nt=1001 at 4 ms, fold uniform in [200, 3000],
     offsets in a 3 km disc restricted to a random azimuth sector 90-360
     degrees wide, model 64 q x 24 azimuths, events as in paper_gather.  Each cube
-    draws from its own seed so any subset can be regenerated alone."""
+    draws from its own seed so any subset can be regenerated alone; with
+    with_data=False only the geometry is drawn (the same offsets, no data)."""
     out = []
     idx = range(ncube) if cubes is None else cubes
     nt, dt, nq, nth = 1001, 0.004, 64, 24
@@ -205,9 +207,11 @@ def cube_batch(seed: int = 3, ncube: int = 512, cubes: Optional[List[int]] = Non
         width = np.deg2rad(rng.uniform(90.0, 360.0))
         start = rng.uniform(0.0, 2.0 * np.pi)
         hx, hy = disc_offsets(rng, fold, 3000.0, start, width)
-        d, ev = hyperbolic_events(rng, nt, dt, hx, hy, 30, (0.2, 3.8),
-                                  (1600.0, 3300.0), (0.0, 0.2), (15.0, 40.0))
-        d = add_noise(rng, d, 0.10)
+        d = None
+        if with_data:
+            d, ev = hyperbolic_events(rng, nt, dt, hx, hy, 30, (0.2, 3.8),
+                                      (1600.0, 3300.0), (0.0, 0.2), (15.0, 40.0))
+            d = add_noise(rng, d, 0.10)
         out.append(Gather(nt, dt, nt, nq, q0, dq, nth, hx, hy, d=d,
                           info=dict(name=f"cube{c}", fold=fold)))
     return out
