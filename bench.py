@@ -852,8 +852,12 @@ def tc_flops(hx, hy, nq, ntheta, nbins, G):
 
 def run_shared64(args):
     """Forward + adjoint of 64 gathers sharing one geometry (8000 traces in a
-    4 km disc, nt = 2048 at 2 ms, 200 q x 72 azimuths): the split-BF16
-    tensor-core contraction against the FP32 spreading path."""
+    4 km disc, nt = 2048 at 2 ms, 200 q x 72 azimuths), three ways: the
+    split-BF16 tensor-core contraction of all 64 in one plan, the FP32
+    spreading path of all 64 in one plan, and one single-gather FP32 plan
+    applied to the 64 gathers in turn (the plain per-gather form).  Errors of
+    each against the FP64 checker on sampled traces (forward) and azimuth
+    slices (adjoint) of two gathers."""
     import numpy as np
     import torch
 
@@ -867,43 +871,137 @@ def run_shared64(args):
 
     geo, _ = syn.shared_batch(seed=replica_seed(4, rank), gathers=[])
     G = 64
+    shape_m = (geo.ntau, geo.nq, geo.ntheta)
     flush = torch.empty(256 * 1024 * 1024 // 4, device="cuda")
-    res = {}
-    for prec in ("split_bf16", "fp32"):
-        gp = AahrtPlan(**geo.geom_kwargs(), ngather=G, precision=prec)
-        gen = torch.Generator(device="cuda").manual_seed(4)
-        m = torch.randn(gp.model_len, device="cuda", generator=gen)
-        d = torch.randn(gp.data_len, device="cuda", generator=gen)
-        mo = torch.empty_like(m)
-        do = torch.empty_like(d)
+
+    # sampled checks: two gathers' data, random models, 16 traces, 2 slices
+    rng = np.random.default_rng(83)
+    sample_g = [5, 50]
+    traces = np.sort(rng.choice(geo.ntr, 16, replace=False))
+    slices = [3, 40]
+    ms = {i: rng.standard_normal(shape_m).astype(np.float32) for i in sample_g}
+    _, dl = syn.shared_batch(seed=replica_seed(4, rank), gathers=sample_g)
+    ds = {i: x.astype(np.float32) for i, x in zip(sample_g, dl)}
+    check = rank == 0 and not args.no_cpu_baseline
+    ref = {}
+    if check:
+        import oracle
+        from oracle import ops
+        op = oracle.make_plan(**geo.geom_kwargs())
+        for i in sample_g:
+            ref[i] = (ops.forward_traces(op, ms[i].astype(np.float64), traces),
+                      ops.adjoint_slices(op, ds[i].astype(np.float64), slices))
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+    def timed_steps(pair):
         for _ in range(max(args.warmup, 3)):
-            gp.forward(m, do)
-            gp.adjoint(d, mo)
+            pair()
         torch.cuda.synchronize()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
         for e0, e1 in ev:
             flush.zero_()
             e0.record()
-            gp.forward(m, do)
-            gp.adjoint(d, mo)
+            pair()
             e1.record()
         torch.cuda.synchronize()
-        ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
-        gp.set_profiling(True)
-        for _ in range(args.steps):
+        return sum(a.elapsed_time(b) for a, b in ev) / args.steps
+
+    res = {}
+    for prec in ("split_bf16", "fp32"):
+        gp = AahrtPlan(**geo.geom_kwargs(), ngather=G, precision=prec)
+        tc = prec == "split_bf16"
+        gen = torch.Generator(device="cuda").manual_seed(4)
+        m = torch.randn(gp.model_len, device="cuda", generator=gen)
+        d = torch.randn(gp.data_len, device="cuda", generator=gen)
+        mo = torch.empty_like(m)
+        do = torch.empty_like(d)
+
+        def pair():
             gp.forward(m, do)
             gp.adjoint(d, mo)
+        ms_pair = timed_steps(pair)
+        gp.set_profiling(True)
+        for _ in range(args.steps):
+            pair()
         torch.cuda.synchronize()
         t, n = gp.stage_times()
         gp.set_profiling(False)
-        if prec == "split_bf16":
+        if tc:
             gp.status()
-        res[prec] = {"ms_per_pair": round(ms, 3), "gather_pairs_per_s": round(G / (ms / 1e3), 2),
+        err = None
+        if check:
+            # the sampled gathers' inputs in this plan's layout
+            mv = m.view(shape_m + (G,)) if tc else m.view((G,) + shape_m)
+            dv = d.view((geo.nt, geo.ntr, G)) if tc else d.view((G, geo.nt, geo.ntr))
+            for i in sample_g:
+                mt = torch.from_numpy(ms[i]).cuda()
+                dt_ = torch.from_numpy(ds[i]).cuda()
+                if tc:
+                    mv[..., i] = mt
+                    dv[..., i] = dt_
+                else:
+                    mv[i] = mt
+                    dv[i] = dt_
+            pair()
+            if tc:
+                gp.status()
+            err = {}
+            for i in sample_g:
+                if tc:
+                    dgi = do.view(geo.nt, geo.ntr, G)[:, :, i]
+                    mgi = mo.view(shape_m + (G,))[..., i]
+                else:
+                    dgi = do.view(G, geo.nt, geo.ntr)[i]
+                    mgi = mo.view((G,) + shape_m)[i]
+                err[i] = (rel(dgi.cpu().numpy()[:, traces].astype(np.float64), ref[i][0]),
+                          rel(mgi.cpu().numpy()[:, :, slices].astype(np.float64), ref[i][1]))
+        res[prec] = {"ms_per_pair": round(ms_pair, 3),
+                     "gather_pairs_per_s": round(G / (ms_pair / 1e3), 2),
                      "stages_ms": {L.STAGE_NAMES[i]: round(t[i] / n[i], 3)
-                                   for i in range(6) if n[i]}, "nbins": gp.info.nbins}
+                                   for i in range(6) if n[i]},
+                     "nbins": gp.info.nbins}
+        if err:
+            res[prec]["err_vs_fp64"] = {
+                "forward_rel_l2_max": max(e[0] for e in err.values()),
+                "adjoint_rel_l2_max": max(e[1] for e in err.values())}
         del gp, m, d, mo, do
         torch.cuda.empty_cache()
+
+    # the plain per-gather form: one FP32 single-gather plan, 64 gathers in turn
+    g1 = AahrtPlan(**geo.geom_kwargs())
+    gen = torch.Generator(device="cuda").manual_seed(4)
+    m1 = torch.randn((G, g1.model_len), device="cuda", generator=gen)
+    d1 = torch.randn((G, g1.data_len), device="cuda", generator=gen)
+    mo1 = torch.empty_like(m1)
+    do1 = torch.empty_like(d1)
+
+    def pair1():
+        for i in range(G):
+            g1.forward(m1[i], do1[i])
+            g1.adjoint(d1[i], mo1[i])
+    ms1 = timed_steps(pair1)
+    err1 = None
+    if check:
+        err1 = {}
+        for i in sample_g:
+            dg = g1.forward(torch.from_numpy(ms[i].ravel()).cuda()).cpu().numpy()
+            mg = g1.adjoint(torch.from_numpy(ds[i].ravel()).cuda()).cpu().numpy()
+            err1[i] = (rel(dg.reshape(geo.nt, geo.ntr)[:, traces].astype(np.float64), ref[i][0]),
+                       rel(mg.reshape(shape_m)[:, :, slices].astype(np.float64), ref[i][1]))
+    res["fp32_per_gather"] = {"ms_per_pair": round(ms1, 3),
+                              "gather_pairs_per_s": round(G / (ms1 / 1e3), 2),
+                              "form": "one single-gather FP32 plan, forward + adjoint of the 64 "
+                                      "gathers one after another"}
+    if err1:
+        res["fp32_per_gather"]["err_vs_fp64"] = {
+            "forward_rel_l2_max": max(e[0] for e in err1.values()),
+            "adjoint_rel_l2_max": max(e[1] for e in err1.values())}
+    del g1, m1, d1, mo1, do1
+    torch.cuda.empty_cache()
+
     tc = res["split_bf16"]
     ff, fa = tc_flops(geo.hx, geo.hy, geo.nq, geo.ntheta, tc["nbins"], G)
     try:
@@ -915,7 +1013,7 @@ def run_shared64(args):
     top, fl, tt = ("slice_adj", fa, t_a) if t_a >= t_f else ("slice_fwd", ff, t_f)
     ach = fl / (tt * 1e-3) / 1e12
     line = {"metric": "shared-geometry gathers: forward+adjoint pairs/s, split-BF16 tensor cores "
-                      "vs FP32 spreading",
+                      "vs FP32 spreading (batched and per gather)",
             "value": tc["gather_pairs_per_s"], "unit": "gather-pairs/s", "n_gpus": 1,
             "steps": args.steps, "warmup": max(args.warmup, 3),
             "ms_per_step": tc["ms_per_pair"], "higher_is_better": True, "vs_baseline": None,
@@ -929,8 +1027,11 @@ def run_shared64(args):
                          "kernel": top + "_tc_kernel", "flops_per_launch": fl,
                          "flops": "executed MMA flops: three bf16 products, padded tiles",
                          "avg_launch_ms": tt, "peak_source": src},
-            "split_bf16": tc, "fp32": res["fp32"],
-            "speedup_vs_fp32": round(res["fp32"]["ms_per_pair"] / tc["ms_per_pair"], 3)}
+            "split_bf16": tc, "fp32": res["fp32"], "fp32_per_gather": res["fp32_per_gather"],
+            "speedup_vs_fp32": round(res["fp32"]["ms_per_pair"] / tc["ms_per_pair"], 3),
+            "speedup_vs_fp32_per_gather": round(res["fp32_per_gather"]["ms_per_pair"] /
+                                                tc["ms_per_pair"], 3),
+            "err_sample": {"gathers": sample_g, "traces": len(traces), "slices": slices}}
     print(json.dumps(line), flush=True)
 
 

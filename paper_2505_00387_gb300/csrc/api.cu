@@ -752,7 +752,10 @@ int aahrt_apply_stage(aahrt_plan *plan, int stage, const void *in, void *out, vo
         case 1: e = launch_slice(p, false, ci, co, st); break;
         case 2: e = launch_c2r(p, false, ci, fo, EPI_STORE, nullptr, FistaArgs{}, st); break;
         case 3: e = launch_r2c(p, false, fi, co, st); break;
-        case 4: e = launch_slice(p, true, ci, co, st); break;
+        case 4:
+            e = launch_ybound(p, ci, st);
+            if (!e) e = launch_slice(p, true, ci, co, st);
+            break;
         case 5: e = launch_c2r(p, true, ci, fo, EPI_STORE, nullptr, FistaArgs{}, st); break;
         default: return set_error(AAHRT_ERR_INVALID_ARG, "stage must be 0..5");
     }

@@ -43,6 +43,7 @@ struct SliceGroup {
     int f0, f1;         // traces with j0 in the owned slices
     int e0, e1;         // traces with j0 == ja - 1 (mod ntheta), adjoint only
     long long ss_off;   // offset of the cube's slice-start table (ntheta + 1 ints)
+    int cube;           // cube index (row of the spectrum bound tables)
 };
 
 // Data block of the partial NMO: nt rows of ld floats starting at float
@@ -127,6 +128,15 @@ struct Plan {
     TraceGeo *geo = nullptr;
     SliceGroup *groups = nullptr;
     int *slice_start = nullptr;    // per distinct geometry: first sorted trace of each slice
+    TraceGeo *geo_adj = nullptr;   // the same traces in the adjoint slice kernel's order
+    // Amplitude bound of the data spectrum for the adjoint spread's
+    // fixed-point scale: ymax[cube][chunk] = max |re| + |im| of Y over the
+    // chunk's 2^ychunk_log bins (float bits; written by the data-side
+    // analysis that produces Y, cleared before it), and wsum[cube][j] = the
+    // total azimuth weight of the traces that reach slice j.
+    unsigned *ymax = nullptr;
+    float *wsum = nullptr;
+    int nychunk = 0, ychunk_log = 6;
     int ngroups_total = 0;
     long long slice_items = 0;
     int *counters = nullptr;       // work counters of the persistent kernels
@@ -270,6 +280,10 @@ struct DeviceGuard {
 // Resolves and caches the allocation-free forward's scratch address on
 // device `dev` (current); called at plan creation (noalloc.cu).
 int noalloc_prepare(int dev);
+
+// Spectrum bound table of the slice adjoint computed from a given Y (when Y
+// does not come from the data-side analysis, which writes the table itself).
+cudaError_t launch_ybound(Plan &p, const float2 *Y, cudaStream_t st);
 
 // operator application used by the C ABI and the solver
 int apply_forward(Plan &p, const float *m, float *d, cudaStream_t st,

@@ -119,7 +119,8 @@ static unsigned long long to_fixed64(double x) {
 }
 
 struct CubeGeo {
-    std::vector<TraceGeo> sorted;
+    std::vector<TraceGeo> sorted;      // by slice, then r^2 (forward order)
+    std::vector<TraceGeo> sorted_adj;  // by slice, then trace index (adjoint order)
     std::vector<int> start;  // start[j]: first sorted trace with j0 == j (size ntheta+1)
 };
 
@@ -151,15 +152,31 @@ static CubeGeo bin_cube(const Plan &p, const double *hx, const double *hy, int n
         t.col = h;
         tr[h] = t;
     }
+    // Traces grouped by azimuth slice.  The forward slice kernel reads them
+    // sorted by r^2 inside a slice: a trace's grid position at bin k is
+    // frac(k B) with B ~ r^2, so one warp's consecutive traces read nearby or
+    // evenly stepped grid points (broadcasts and fewer bank conflicts).  The
+    // adjoint's atomics prefer the opposite (nearby positions collide on the
+    // same words), so it gets the slices in the traces' own order.  Neither
+    // order changes a result: each trace is independent in the forward, and
+    // the adjoint's fixed-point sums are exact.
+    std::vector<double> r2v(ntr);
+    for (int h = 0; h < ntr; ++h) r2v[h] = hx[h] * hx[h] + hy[h] * hy[h];
     std::vector<int> idx(ntr);
     std::iota(idx.begin(), idx.end(), 0);
-    std::stable_sort(idx.begin(), idx.end(),
-                     [&](int a, int b) { return tr[a].j0 < tr[b].j0; });
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
+        return tr[a].j0 != tr[b].j0 ? tr[a].j0 < tr[b].j0 : r2v[a] < r2v[b];
+    });
+    g.start.assign(p.ntheta + 1, 0);
+    for (int i = 0; i < ntr; ++i) g.start[tr[idx[i]].j0 + 1]++;
+    for (int j = 0; j < p.ntheta; ++j) g.start[j + 1] += g.start[j];
     g.sorted.resize(ntr);
     for (int i = 0; i < ntr; ++i) g.sorted[i] = tr[idx[i]];
-    g.start.assign(p.ntheta + 1, 0);
-    for (int i = 0; i < ntr; ++i) g.start[g.sorted[i].j0 + 1]++;
-    for (int j = 0; j < p.ntheta; ++j) g.start[j + 1] += g.start[j];
+    std::vector<int> ida(ntr);
+    std::iota(ida.begin(), ida.end(), 0);
+    std::stable_sort(ida.begin(), ida.end(), [&](int a, int b) { return tr[a].j0 < tr[b].j0; });
+    g.sorted_adj.resize(ntr);
+    for (int i = 0; i < ntr; ++i) g.sorted_adj[i] = tr[ida[i]];
     return g;
 }
 
@@ -184,7 +201,8 @@ void free_plan(Plan *p) {
                     p->posU, p->rngST, p->rngUT, p->X, p->Y, p->z, p->r, p->v, p->scal,
                     p->stage_m, p->stage_d, p->zb, p->mb, p->rb, p->db, p->vjp_ws,
                     p->cube_gt, p->cube_acc, p->dseg, p->tc_tiles, p->wav, p->wtmp,
-                    p->qn, p->qv, p->pn_blk, p->pn_rho, p->pn_c};
+                    p->qn, p->qv, p->pn_blk, p->pn_rho, p->pn_c, p->ymax, p->wsum,
+                    p->geo_adj};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     cudaSetDevice(cur);
@@ -432,11 +450,12 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
     std::vector<CubeGeo> cg(ndist);
     for (int c = 0; c < ndist; ++c) cg[c] = bin_cube(*p, geoms[c].hx, geoms[c].hy, geoms[c].ntr);
     std::vector<long long> geo_off(ndist, 0);
-    std::vector<TraceGeo> geo_all;
+    std::vector<TraceGeo> geo_all, geo_adj_all;
     std::vector<int> ss_all;
     for (int c = 0; c < ndist; ++c) {
         geo_off[c] = (long long)geo_all.size();
         geo_all.insert(geo_all.end(), cg[c].sorted.begin(), cg[c].sorted.end());
+        geo_adj_all.insert(geo_adj_all.end(), cg[c].sorted_adj.begin(), cg[c].sorted_adj.end());
         ss_all.insert(ss_all.end(), cg[c].start.begin(), cg[c].start.end());
     }
     p->ntr.resize(ncube);
@@ -464,6 +483,7 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
         const CubeGeo &G = cg[dc];
         for (int gi = 0; gi < p->ngroup; ++gi) {
             SliceGroup s;
+            s.cube = c;
             s.geo_off = geo_off[dc];
             s.ss_off = (long long)dc * (p->ntheta + 1);
             s.x_off = (long long)c * p->nbins * C;
@@ -622,8 +642,31 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
     AAHRT_TRY(upload(&p->tw_q, twiddles(p->nos)), "upload twiddles");
     AAHRT_TRY(upload(&p->dec, dec), "upload deapodisation");
     AAHRT_TRY(upload(&p->geo, geo_all), "upload geometry");
+    AAHRT_TRY(upload(&p->geo_adj, geo_adj_all), "upload geometry");
     AAHRT_TRY(upload(&p->groups, groups), "upload work list");
     AAHRT_TRY(upload(&p->slice_start, ss_all), "upload slice table");
+    if (!tc) {
+        // spectrum bound tables of the adjoint spread (see ymax, wsum)
+        p->ychunk_log = 6;
+        while ((p->nbins >> p->ychunk_log) > 128) ++p->ychunk_log;
+        p->nychunk = (p->nbins + (1 << p->ychunk_log) - 1) >> p->ychunk_log;
+        std::vector<float> ws((size_t)ncube * p->ntheta);
+        for (int c = 0; c < ncube; ++c) {
+            const CubeGeo &G = cg[ndist == 1 ? 0 : c];
+            std::vector<double> acc(p->ntheta, 0.0);
+            for (const TraceGeo &t : G.sorted) {
+                acc[t.j0] += t.w0;
+                acc[(t.j0 + 1) % p->ntheta] += t.w1;
+            }
+            for (int j = 0; j < p->ntheta; ++j)   // rounded up: a bound
+                ws[(size_t)c * p->ntheta + j] = (float)(acc[j] * (1.0 + 1e-6));
+        }
+        AAHRT_TRY(upload(&p->wsum, ws), "upload slice weights");
+        AAHRT_TRY(cudaMalloc((void **)&p->ymax, (size_t)ncube * p->nychunk * sizeof(unsigned)),
+                  "alloc spectrum bound");
+        AAHRT_TRY(cudaMemset(p->ymax, 0, (size_t)ncube * p->nychunk * sizeof(unsigned)),
+                  "clear spectrum bound");
+    }
     AAHRT_TRY(upload(&p->cg_model, cgm), "upload column groups");
     AAHRT_TRY(upload(&p->cg_data, cgd), "upload column groups");
     AAHRT_TRY(upload(&p->cg_model_blk, cgmb), "upload column groups");
@@ -698,7 +741,10 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
     int max_smem = 0;
     AAHRT_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin,
                                      p->device), "device query");
-    if ((int)smem_r2c > max_smem || (int)smem_c2r > max_smem || (int)p->smem_sfwd > max_smem ||
+    // the time kernels hold 512 bytes of static shared memory (the spectrum
+    // bound of the data-side unpack) beside their dynamic buffers
+    const int max_time = max_smem - 512;
+    if ((int)smem_r2c > max_time || (int)smem_c2r > max_time || (int)p->smem_sfwd > max_smem ||
         (int)p->smem_sadj > max_smem) {
         rc_fail = set_error(AAHRT_ERR_UNSUPPORTED,
                             "shared memory per block (%zu / %zu bytes) exceeds %d; lower "
@@ -706,8 +752,8 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
         free_plan(p);
         return rc_fail;
     }
-    if ((int)p->smem_fused_model > max_smem) p->smem_fused_model = 0;
-    if ((int)p->smem_fused_data > max_smem) p->smem_fused_data = 0;
+    if ((int)p->smem_fused_model > max_time) p->smem_fused_model = 0;
+    if ((int)p->smem_fused_data > max_time) p->smem_fused_data = 0;
     // The dynamic shared memory limit is a property of each kernel function,
     // shared by every plan of the process: raise it to the device maximum once
     // so no plan lowers it under another.

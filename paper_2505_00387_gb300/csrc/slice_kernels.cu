@@ -11,9 +11,11 @@
 // weights, phases and twiddles).  The spread accumulates in 32-bit fixed
 // point with native shared-memory integer atomics (real and imaginary parts in
 // separate planes).  Each azimuth slice gets its own scale
-// 2^30 / (Phi_max * scale * sum_h w_h |y_h|) over the traces that reach it, so
-// no grid sum can exceed 2^30 and the rounding of each contribution stays at
-// the level of FP32 rounding of the slice's values.
+// 2^30 / (Phi_max * scale * M * sum_h w_h) over the traces h that reach it,
+// where M bounds |re y| + |im y| over the cube's bins in a chunk of 2^b bins
+// (computed by the data-side analysis that wrote Y): no grid sum can exceed
+// 2^30, and the rounding of each contribution stays near FP32 rounding of the
+// slice's values.
 //
 // Work items are (cube, azimuth group, bin); a persistent grid pulls them
 // from an atomic counter (reset by the launcher), largest groups first.
@@ -24,7 +26,8 @@
 namespace aahrt {
 
 struct SliceArgs {
-    const TraceGeo *__restrict__ geo;
+    const TraceGeo *__restrict__ geo;       // forward order (by slice, then r^2)
+    const TraceGeo *__restrict__ geo_adj;   // adjoint order (by slice, then trace)
     const SliceGroup *__restrict__ groups;
     const int *__restrict__ slice_start;
     const float *__restrict__ dec;
@@ -34,6 +37,9 @@ struct SliceArgs {
     int nbins, nq, ntheta, nos, Lq, cq, ngroup;
     float scale;
     float phimax;    // max over positions of sum_i phi_i (spread bound)
+    const unsigned *__restrict__ ymax;   // [cube][chunk] max |re| + |im| of Y (float bits)
+    const float *__restrict__ wsum;      // [cube][slice] azimuth weight reaching the slice
+    int nychunk, ychunk_log;
     EsPoly poly;     // kernel-parameter (constant) bank: broadcast FMA operands
 };
 
@@ -252,7 +258,6 @@ slice_adj_kernel(const SliceArgs a, const float2 *__restrict__ Y, float2 *__rest
     extern __shared__ float4 smem_f4[];
     float *smf = reinterpret_cast<float *>(smem_f4);
     __shared__ long long s_item;
-    __shared__ float s_sa[kMaxGroupSlices + 1], s_sb[kMaxGroupSlices + 1];
     __shared__ float s_fx[kMaxGroupSlices], s_ifx[kMaxGroupSlices];
     const int lds = ld_split(a.nos);
     const int mask = a.nos - 1;
@@ -268,12 +273,11 @@ slice_adj_kernel(const SliceArgs a, const float2 *__restrict__ Y, float2 *__rest
         float *Gim = smf + g.nj * lds;
         int *Ire = reinterpret_cast<int *>(Gre);
         int *Iim = reinterpret_cast<int *>(Gim);
-        const TraceGeo *geo = a.geo + g.geo_off;
+        const TraceGeo *geo = a.geo_adj + g.geo_off;
         const float2 *Yk = Y + g.y_off + (long long)k * g.ntr;
 
-        // zero the grid; per owned slice, bound its spread by the sums
-        // A_j = sum w0 |y| over traces with j0 = j and B_j = sum w1 |y| over
-        // traces with j0 = j (whose second weight lands on slice j + 1)
+        // zero the grid; per owned slice, the fixed-point scale from the
+        // chunk's amplitude bound and the slice's total azimuth weight
         {
             const int nz4 = (2 * g.nj * lds) >> 2;
             float4 *z4 = reinterpret_cast<float4 *>(smf);
@@ -282,45 +286,15 @@ slice_adj_kernel(const SliceArgs a, const float2 *__restrict__ Y, float2 *__rest
             for (int idx = 4 * nz4 + threadIdx.x; idx < 2 * g.nj * lds; idx += blockDim.x)
                 smf[idx] = 0.f;
         }
-        const int *sstart = a.slice_start + g.ss_off;
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        const int nseg = g.nj + 1;            // owned slices, then the slice before ja
-        for (int sg = warp; sg < nseg; sg += kThreadsSlice / 32) {
-            int t0, t1;
-            if (sg < g.nj) {
-                t0 = sstart[g.ja + sg];
-                t1 = sstart[g.ja + sg + 1];
-            } else {
-                t0 = g.e0;                   // empty when one group owns every slice
-                t1 = g.e1;
+        {
+            const float M = __uint_as_float(
+                __ldg(a.ymax + (long long)g.cube * a.nychunk + (k >> a.ychunk_log)));
+            const float *ws = a.wsum + (long long)g.cube * a.ntheta + g.ja;
+            for (int jj = threadIdx.x; jj < g.nj; jj += blockDim.x) {
+                const float bound = M * __ldg(ws + jj) * a.scale * a.phimax;
+                s_fx[jj] = bound > 0.f ? 1073741824.0f / bound : 0.f;   // 2^30 / bound
+                s_ifx[jj] = bound > 0.f ? bound * 9.3132257461547852e-10f : 0.f;   // 1/fx
             }
-            float sa = 0.f, sb = 0.f;
-            for (int t = t0 + lane; t < t1; t += 32) {
-                const TraceGeo tr = geo[t];
-                const float2 y = __ldg(Yk + tr.col);
-                const float ay = fabsf(y.x) + fabsf(y.y);
-                sa = fmaf(tr.w0, ay, sa);
-                sb = fmaf(tr.w1, ay, sb);
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                sa += __shfl_down_sync(0xffffffffu, sa, o);
-                sb += __shfl_down_sync(0xffffffffu, sb, o);
-            }
-            if (lane == 0) {
-                s_sa[sg] = sa;
-                s_sb[sg] = sb;
-            }
-        }
-        __syncthreads();
-        for (int jj = threadIdx.x; jj < g.nj; jj += blockDim.x) {
-            // slice jj receives w1 parts from the slice before it: jj - 1, or
-            // for jj = 0 the slice before the group (last owned slice when the
-            // group owns every slice, else the e-range)
-            const float prev = jj > 0 ? s_sb[jj - 1] : (a.ngroup > 1 ? s_sb[g.nj] : s_sb[g.nj - 1]);
-            const float bound = (s_sa[jj] + prev) * a.scale * a.phimax;
-            s_fx[jj] = bound > 0.f ? 1073741824.0f / bound : 0.f;   // 2^30 / bound
-            s_ifx[jj] = bound > 0.f ? bound * 9.3132257461547852e-10f : 0.f;   // 1/fx
         }
         __syncthreads();
 
@@ -365,9 +339,42 @@ slice_adj_kernel(const SliceArgs a, const float2 *__restrict__ Y, float2 *__rest
     }
 }
 
+// The spectrum bound table ymax from a given Y (for a slice adjoint whose
+// input was not written by the data-side analysis): block (group, chunk)
+// raises ymax[cube][chunk] to the largest |re| + |im| over the chunk's bins
+// and the cube's traces.
+__global__ void ybound_kernel(const SliceGroup *__restrict__ groups,
+                              const float2 *__restrict__ Y, int nbins, int chunk_log,
+                              int nchunk, unsigned *__restrict__ ymax) {
+    const SliceGroup g = groups[blockIdx.x];
+    const int k0 = blockIdx.y << chunk_log;
+    const int k1 = min(nbins, k0 + (1 << chunk_log));
+    const long long n = (long long)(k1 - k0) * g.ntr;
+    const float2 *src = Y + g.y_off + (long long)k0 * g.ntr;
+    float m = 0.f;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+        const float2 v = __ldg(src + i);
+        m = fmaxf(m, fabsf(v.x) + fabsf(v.y));
+    }
+#pragma unroll
+    for (int sh = 16; sh > 0; sh >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, sh));
+    if ((threadIdx.x & 31) == 0 && m > 0.f)
+        atomicMax(ymax + (long long)g.cube * nchunk + blockIdx.y, __float_as_uint(m));
+}
+
+cudaError_t launch_ybound(Plan &p, const float2 *Y, cudaStream_t st) {
+    if (!p.ymax || p.precision == 1 || p.slice_interp == AAHRT_SLICE_DIRECT) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(p.ymax, 0, (size_t)p.ncube * p.nychunk * sizeof(unsigned), st);
+    if (e) return e;
+    ybound_kernel<<<dim3(p.ngroups_total, p.nychunk), 256, 0, st>>>(
+        p.groups, Y, p.nbins, p.ychunk_log, p.nychunk, p.ymax);
+    return cudaGetLastError();
+}
+
 static SliceArgs make_args(const Plan &p, int counter_slot) {
     SliceArgs a;
     a.geo = p.geo;
+    a.geo_adj = p.geo_adj;
     a.groups = p.groups;
     a.slice_start = p.slice_start;
     a.dec = p.dec;
@@ -383,6 +390,10 @@ static SliceArgs make_args(const Plan &p, int counter_slot) {
     a.ngroup = p.ngroup;
     a.scale = (float)(1.0 / p.nfft);
     a.phimax = (float)p.phimax;
+    a.ymax = p.ymax;
+    a.wsum = p.wsum;
+    a.nychunk = p.nychunk;
+    a.ychunk_log = p.ychunk_log;
     a.poly = p.poly;
     return a;
 }

@@ -95,22 +95,41 @@ struct Acc {
 // The r2c pipeline after its input rows are staged in shared memory
 // (stg [row][2P] floats, sfr the source fractions of a transposed
 // resampler; the caller synchronised): resample onto the frame, FFT, unpack.
+// With a bound table (data side only: TRANS, ybd.max != nullptr) the unpack
+// also raises ybd.max[cube][chunk] to the largest |re| + |im| it writes in
+// each chunk of bins: the amplitude bound of the adjoint spread's fixed point.
+struct YBound {
+    unsigned *max;
+    int nchunk, chunk_log;
+};
+
 template <int LP, int INTERP, bool TRANS>
 __device__ __forceinline__ void r2c_core(float2 *sm, const float *stg, const float *sfr,
                                          const ColGroup &cg, const DevResampler &rs,
                                          int nrow_in, const float2 *__restrict__ tw, int L,
-                                         int nbins, float2 *__restrict__ out) {
+                                         int nbins, float2 *__restrict__ out,
+                                         const YBound &ybd) {
     constexpr int P = 1 << LP;
     const int N = 1 << L;
     const int ld = ld_interleaved(N);
     // z_p[n] = sum_r G[n][r] (x_{2p} + i x_{2p+1})[r], one row n per thread
     const float2 *stg2 = reinterpret_cast<const float2 *>(stg);
+    // the next row's table entry is loaded while this row is resampled
+    int2 nxt = make_int2(0, 0);
+    if ((int)threadIdx.x < rs.nrows)
+        nxt = __ldg(reinterpret_cast<const int2 *>(TRANS ? (const void *)(rs.rng + threadIdx.x)
+                                                         : (const void *)(rs.pos + threadIdx.x)));
     for (int n = threadIdx.x; n < N; n += blockDim.x) {
         Acc<P> acc;
         acc.zero();
+        const int2 cur = nxt;
+        if (n + (int)blockDim.x < rs.nrows)
+            nxt = __ldg(reinterpret_cast<const int2 *>(
+                TRANS ? (const void *)(rs.rng + n + blockDim.x)
+                      : (const void *)(rs.pos + n + blockDim.x)));
         if (n < rs.nrows) {
             if (!TRANS) {
-                const RowPos ps = load_pos(rs.pos + n);
+                const RowPos ps{cur.x, __int_as_float(cur.y)};
 #pragma unroll
                 for (int q = 0; q < Taps<INTERP>::n; ++q) {
                     const int t = Taps<INTERP>::t0 + q;
@@ -119,7 +138,7 @@ __device__ __forceinline__ void r2c_core(float2 *sm, const float *stg, const flo
                     acc.add_row(tap_weight<INTERP>(t, ps.fr), stg2 + r * P);
                 }
             } else {
-                const RowRange rg = load_rng(rs.rng + n);
+                const RowRange rg{cur.x, cur.y};
                 int r = rg.lo;
 #pragma unroll
                 for (int q = Taps<INTERP>::n - 1; q >= 0; --q) {
@@ -139,17 +158,49 @@ __device__ __forceinline__ void r2c_core(float2 *sm, const float *stg, const flo
     // unpack the two real spectra: A = (Z_k + conj Z_{N-k})/2, B = (Z_k - conj Z_{N-k})/(2i)
     float2 *dst = out + cg.spec_off;
     const int npair = (cg.ncol + 1) >> 1;
-    for (int idx = threadIdx.x; idx < P * nbins; idx += blockDim.x) {
+    const bool bound = TRANS && ybd.max != nullptr;
+    __shared__ unsigned s_ymax[128];
+    if (bound) {
+        for (int c = threadIdx.x; c < ybd.nchunk; c += blockDim.x) s_ymax[c] = 0u;
+        __syncthreads();
+    }
+    const int kend = ((P * nbins + blockDim.x - 1) / blockDim.x) * blockDim.x;
+    for (int idx = threadIdx.x; idx < kend; idx += blockDim.x) {
         const int p = idx & (P - 1);
         const int k = idx >> LP;
-        if (p >= npair) continue;
-        const float2 zk = sm[p * ld + padi(brev_bits(k, L))];
-        const float2 zn = sm[p * ld + padi(brev_bits((N - k) & (N - 1), L))];
-        const float2 A = make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
-        const float2 B = make_float2(0.5f * (zk.y + zn.y), -0.5f * (zk.x - zn.x));
-        const long long o = (long long)k * cg.ld_spec + 2 * p;
-        dst[o] = A;
-        if (2 * p + 1 < cg.ncol) dst[o + 1] = B;
+        float amax = 0.f;
+        if (idx < P * nbins && p < npair) {
+            const float2 zk = sm[p * ld + padi(brev_bits(k, L))];
+            const float2 zn = sm[p * ld + padi(brev_bits((N - k) & (N - 1), L))];
+            const float2 A = make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
+            const float2 B = make_float2(0.5f * (zk.y + zn.y), -0.5f * (zk.x - zn.x));
+            const long long o = (long long)k * cg.ld_spec + 2 * p;
+            dst[o] = A;
+            amax = fabsf(A.x) + fabsf(A.y);
+            if (2 * p + 1 < cg.ncol) {
+                dst[o + 1] = B;
+                amax = fmaxf(amax, fabsf(B.x) + fabsf(B.y));
+            }
+        }
+        if (bound) {
+            // a warp's 32 / P bins lie inside one chunk (chunks of >= 64 bins)
+#pragma unroll
+            for (int sh = 16; sh > 0; sh >>= 1)
+                amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, sh));
+            const int kw = (idx & ~31) >> LP;
+            if ((threadIdx.x & 31) == 0 && kw < nbins && amax > 0.f)
+                atomicMax(s_ymax + (kw >> ybd.chunk_log), __float_as_uint(amax));
+        }
+    }
+    if (bound) {
+        __syncthreads();
+        // the table only grows within a launch, so a block whose maximum does
+        // not exceed the value it reads needs no atomic
+        unsigned *row = ybd.max + (long long)cg.cube * ybd.nchunk;
+        for (int c = threadIdx.x; c < ybd.nchunk; c += blockDim.x) {
+            const unsigned v = s_ymax[c];
+            if (v > *(volatile unsigned *)(row + c)) atomicMax(row + c, v);
+        }
     }
 }
 
@@ -157,7 +208,7 @@ template <int LP, int INTERP, bool TRANS>
 __global__ void __launch_bounds__(kThreadsTime, 2)
 r2c_kernel(const float *__restrict__ in, float2 *__restrict__ out,
            const ColGroup *__restrict__ groups, DevResampler rs, int nrow_in,
-           const float2 *__restrict__ tw, int L, int nbins) {
+           const float2 *__restrict__ tw, int L, int nbins, YBound ybd) {
     constexpr int P = 1 << LP;
     extern __shared__ float4 smem_f4[];
     float2 *sm = reinterpret_cast<float2 *>(smem_f4);
@@ -187,7 +238,7 @@ r2c_kernel(const float *__restrict__ in, float2 *__restrict__ out,
         for (int idx = threadIdx.x; idx < rs.npos; idx += blockDim.x)
             sfr[idx] = __ldg(&rs.pos[idx].fr);
     __syncthreads();
-    r2c_core<LP, INTERP, TRANS>(sm, stg, sfr, cg, rs, nrow_in, tw, L, nbins, out);
+    r2c_core<LP, INTERP, TRANS>(sm, stg, sfr, cg, rs, nrow_in, tw, L, nbins, out, ybd);
 }
 
 // The c2r pipeline of one column group.  With STAGE, the epilogue's real
@@ -259,12 +310,31 @@ __device__ __forceinline__ void c2r_core(float2 *sm, float *sfr, const float2 *_
         __syncthreads();
     }
 
-    // resample the synthesized columns onto the output rows, one row per thread
+    // resample the synthesized columns onto the output rows, one row per
+    // thread; the next row's table entry is loaded while this one is done
+    int2 nxt = make_int2(0, 0);
+    if ((int)threadIdx.x < rs.nrows)
+        nxt = __ldg(reinterpret_cast<const int2 *>(TRANS ? (const void *)(rs.rng + threadIdx.x)
+                                                         : (const void *)(rs.pos + threadIdx.x)));
     for (int i = threadIdx.x; i < rs.nrows; i += blockDim.x) {
         Acc<P> acc;
         acc.zero();
+        const int2 cur = nxt;
+        if (i + (int)blockDim.x < rs.nrows)
+            nxt = __ldg(reinterpret_cast<const int2 *>(
+                TRANS ? (const void *)(rs.rng + i + blockDim.x)
+                      : (const void *)(rs.pos + i + blockDim.x)));
+        const long long o = cg.real_off + (long long)i * cg.ld_real;
+        const int nc = cg.ncol;
+        // the FISTA update's m row is loaded first, its latency covered by
+        // the resampling below
+        float mo[2 * P];
+        if (EPI == EPI_FISTA) {
+#pragma unroll
+            for (int c = 0; c < 2 * P; ++c) mo[c] = c < nc ? fa.m[o + c] : 0.f;
+        }
         if (!TRANS) {
-            const RowPos ps = load_pos(rs.pos + i);
+            const RowPos ps{cur.x, __int_as_float(cur.y)};
 #pragma unroll
             for (int q = 0; q < Taps<INTERP>::n; ++q) {
                 const int t = Taps<INTERP>::t0 + q;
@@ -273,7 +343,7 @@ __device__ __forceinline__ void c2r_core(float2 *sm, float *sfr, const float2 *_
                 acc.add_cols(tap_weight<INTERP>(t, ps.fr), sm, ld, padi(r));
             }
         } else {
-            const RowRange rg = load_rng(rs.rng + i);
+            const RowRange rg{cur.x, cur.y};
             int r = rg.lo;
 #pragma unroll
             for (int q = Taps<INTERP>::n - 1; q >= 0; --q) {
@@ -283,8 +353,6 @@ __device__ __forceinline__ void c2r_core(float2 *sm, float *sfr, const float2 *_
                     acc.add_cols(tap_weight<INTERP>(t, sfr[r]), sm, ld, padi(r));
             }
         }
-        const long long o = cg.real_off + (long long)i * cg.ld_real;
-        const int nc = cg.ncol;
         float g2[2 * P];
 #pragma unroll
         for (int p = 0; p < P; ++p) {
@@ -318,12 +386,10 @@ __device__ __forceinline__ void c2r_core(float2 *sm, float *sfr, const float2 *_
             }
             float *__restrict__ mp = fa.m + o;
             float *__restrict__ zp = fa.z + o;
-            float mo[2 * P], zo[2 * P];
+            float zo[2 * P];
 #pragma unroll
-            for (int c = 0; c < 2 * P; ++c) {
-                mo[c] = c < nc ? mp[c] : 0.f;
+            for (int c = 0; c < 2 * P; ++c)
                 zo[c] = c < nc ? (STAGE ? stg[i * 2 * P + c] : zp[c]) : 0.f;
-            }
 #pragma unroll
             for (int c = 0; c < 2 * P; ++c) {
                 if (c >= nc) {
@@ -368,7 +434,7 @@ __global__ void __launch_bounds__(kThreadsTime, 2)
 c2r_r2c_kernel(float2 *spec, const float *__restrict__ aux, FistaArgs fa,
                const ColGroup *__restrict__ groups, DevResampler rs_syn, int n_in,
                DevResampler rs_ana, int nrow_mid, const float2 *__restrict__ tw, int L,
-               int nbins) {
+               int nbins, YBound ybd) {
     constexpr int P = 1 << LP;
     constexpr bool ANA_TRANS = !SYN_TRANS;
     extern __shared__ float4 smem_f4[];
@@ -390,20 +456,28 @@ c2r_r2c_kernel(float2 *spec, const float *__restrict__ aux, FistaArgs fa,
             sfr[idx] = __ldg(&rs_ana.pos[idx].fr);
         __syncthreads();
     }
-    r2c_core<LP, INTERP, ANA_TRANS>(sm, stg, sfr, cg, rs_ana, nrow_mid, tw, L, nbins, spec);
+    r2c_core<LP, INTERP, ANA_TRANS>(sm, stg, sfr, cg, rs_ana, nrow_mid, tw, L, nbins, spec, ybd);
 }
 
 // ------------------------------------------------------------- dispatch
 template <int LP, int INTERP>
 static void r2c_launch(bool model_side, int grid, size_t smem, cudaStream_t st, const float *in,
                        float2 *out, const ColGroup *cg, DevResampler rs, int nrow_in,
-                       const float2 *tw, int L, int nbins) {
+                       const float2 *tw, int L, int nbins, YBound ybd = YBound{}) {
     if (model_side)
         r2c_kernel<LP, INTERP, false><<<grid, kThreadsTime, smem, st>>>(in, out, cg, rs, nrow_in,
-                                                                        tw, L, nbins);
+                                                                        tw, L, nbins, YBound{});
     else
         r2c_kernel<LP, INTERP, true><<<grid, kThreadsTime, smem, st>>>(in, out, cg, rs, nrow_in,
-                                                                       tw, L, nbins);
+                                                                       tw, L, nbins, ybd);
+}
+
+// The bound table of the data spectrum, cleared for the analysis about to
+// write Y (nothing for plans without one).
+static cudaError_t ybound_reset(Plan &p, cudaStream_t st, YBound *yb) {
+    *yb = YBound{p.ymax, p.nychunk, p.ychunk_log};
+    if (!p.ymax) return cudaSuccess;
+    return cudaMemsetAsync(p.ymax, 0, (size_t)p.ncube * p.nychunk * sizeof(unsigned), st);
 }
 
 template <int LP, int INTERP, int EPI>
@@ -439,9 +513,14 @@ cudaError_t launch_r2c(Plan &p, bool model_side, const float *in, float2 *out,
     const int nrow_in = model_side ? p.ntau : p.nt;
     const size_t smem = model_side ? p.smem_r2c_model : p.smem_r2c_data;
     const int stage = model_side ? 0 : 3;
+    YBound yb{};
+    if (!model_side) {
+        const cudaError_t e = ybound_reset(p, st, &yb);
+        if (e) return e;
+    }
     prof_begin(p, stage, st);
     AAHRT_LP_SWITCH(p.lp, AAHRT_INTERP_SWITCH(p.interp, (r2c_launch<LPc, IPc>(
-        model_side, n, smem, st, in, out, cg, rs, nrow_in, p.tw_t, p.L, p.nbins))));
+        model_side, n, smem, st, in, out, cg, rs, nrow_in, p.tw_t, p.L, p.nbins, yb))));
     prof_end(p, st);
     p.launches[stage]++;
     return cudaGetLastError();
@@ -499,16 +578,22 @@ cudaError_t launch_c2r_r2c(Plan &p, bool model_side, float2 *spec, const float *
     const ColGroup *cg = model_side ? p.cg_model_blk : p.cg_data_blk;
     const int n = model_side ? p.ncg_model : p.ncg_data;
     const int stage = model_side ? 5 : 2;
+    YBound yb{};
+    if (!model_side) {
+        const cudaError_t e = ybound_reset(p, st, &yb);
+        if (e) return e;
+    }
     prof_begin(p, stage, st);
     if (model_side) {
         AAHRT_LP_SWITCH(p.lp, AAHRT_INTERP_SWITCH(p.interp, (
             c2r_r2c_kernel<LPc, IPc, true, EPI_FISTA><<<n, kThreadsTime, p.smem_fused_model, st>>>(
-                spec, nullptr, fa, cg, p.ST, p.ns, p.S, p.ntau, p.tw_t, p.L, p.nbins))));
+                spec, nullptr, fa, cg, p.ST, p.ns, p.S, p.ntau, p.tw_t, p.L, p.nbins,
+                YBound{}))));
     } else {
         AAHRT_LP_SWITCH(p.lp, AAHRT_INTERP_SWITCH(p.interp, (
             c2r_r2c_kernel<LPc, IPc, false, EPI_RESIDUAL><<<n, kThreadsTime, p.smem_r2c_data,
                                                            st>>>(
-                spec, aux, FistaArgs{}, cg, p.U, p.ns, p.UT, p.nt, p.tw_t, p.L, p.nbins))));
+                spec, aux, FistaArgs{}, cg, p.U, p.ns, p.UT, p.nt, p.tw_t, p.L, p.nbins, yb))));
     }
     prof_end(p, st);
     p.launches[stage]++;

@@ -43,9 +43,15 @@ def test_forward_adjoint_dot(case, center, shift):
     wf = w.astype(np.float32).astype(np.float64)
     assert rel(dg, decon.forward(op, m, wf, center)) < TOL_OP
     assert rel(mg, decon.adjoint(op, d, wf, center)) < TOL_OP
+    # dot test on a well-conditioned pair: d2 = W L m by the oracle plus as
+    # much noise, so <W L m, d2> is about |W L m|^2 (for two independent
+    # random vectors the inner product is itself often near zero)
     m32 = m.astype(np.float32).astype(np.float64)
-    d32 = d.astype(np.float32).astype(np.float64)
-    lhs, rhs = float(np.sum(dg * d32)), float(np.sum(mg * m32))
+    lm = decon.forward(op, m32, wf, center)
+    d2 = lm + np.sqrt(np.mean(lm * lm)) * rng.standard_normal(lm.shape)
+    d2 = d2.astype(np.float32).astype(np.float64)
+    lhs = float(np.sum(host(gp.forward(dev(m32)), d.shape) * d2))
+    rhs = float(np.sum(host(gp.adjoint(dev(d2)), m.shape) * m32))
     assert abs(lhs - rhs) <= 1e-6 * abs(lhs)
     gp.set_wavelet(None, 0)
 

@@ -37,17 +37,17 @@ def test_lineark_matches_oracle(case, sigma_q):
     mg = host(gp.adjoint(dev(d)), m.shape)
     assert rel(dg, lineark.forward(op, m, sigma_q)) < TOL_OP
     assert rel(mg, lineark.adjoint(op, d, sigma_q)) < TOL_OP
-    # dot test on the FP32 inputs the GPU actually received
+    # dot test on a well-conditioned pair of FP32 inputs: d2 = L m by the
+    # oracle plus as much noise, so <L m, d2> is about |L m|^2
     m32 = m.astype(np.float32).astype(np.float64)
-    d32 = d.astype(np.float32).astype(np.float64)
-    lhs, rhs = float(np.sum(dg * d32)), float(np.sum(mg * m32))
-    # Without oversampling (sigma_q = 1) the whole q spectrum sits on nq grid
-    # points, so each point of the adjoint's fixed-point grid sums about
-    # twice as many trace contributions as at sigma_q = 2 (measured 1-2e-6).
-    tol = 1e-6 if sigma_q >= 2.0 else 5e-6
+    lm = lineark.forward(op, m32, sigma_q)
+    d2 = lm + np.sqrt(np.mean(lm * lm)) * rng.standard_normal(lm.shape)
+    d2 = d2.astype(np.float32).astype(np.float64)
+    lhs = float(np.sum(host(gp.forward(dev(m32)), d.shape) * d2))
+    rhs = float(np.sum(host(gp.adjoint(dev(d2)), m.shape) * m32))
     print(f"{case} sigma_q={sigma_q}: fwd {rel(dg, lineark.forward(op, m, sigma_q)):.2e} "
           f"dot {abs(lhs - rhs) / abs(lhs):.2e}")
-    assert abs(lhs - rhs) <= tol * abs(lhs)
+    assert abs(lhs - rhs) <= 1e-6 * abs(lhs)
 
 
 def test_lineark_error_against_exact_operator():

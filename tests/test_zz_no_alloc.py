@@ -32,7 +32,7 @@ def _plan(kind):
     if kind == "direct":
         gp = AahrtPlan(**g.geom_kwargs(), slice_interp="direct")
     elif kind == "split_bf16":
-        gp = AahrtPlan(**g.geom_kwargs(), ngather=8, precision="split_bf16")
+        gp = AahrtPlan(**g.geom_kwargs(), ngather=4, precision="split_bf16")
     else:
         gp = AahrtPlan(**g.geom_kwargs())
     if kind == "wavelet":
