@@ -13,6 +13,10 @@
 namespace aahrt {
 
 constexpr int kThreadsTime = 256;
+constexpr int kMaxThreadsTime = 512;
+// dynamic shared memory of a time-kernel block up to which two blocks fit on
+// one SM (228 KB per SM, 1 KB reserved per block, 512 bytes static)
+constexpr int kTimeSmemTwoBlocks = 112 * 1024;
 constexpr int kThreadsSlice = 256;
 constexpr int kMinW = 4;
 constexpr int kMaxW = 12;

@@ -22,11 +22,12 @@
 //   A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi   (FP32 accumulation in TMEM).
 // The phase arguments are range-reduced exactly in 64-bit fixed point.
 //
-// One CTA per SM (persistent, items from an atomic counter); all 16 warps
-// build the bf16 operand tiles of a K chunk (64 K-elements) in shared memory
-// (128-byte swizzled K-major layout) while the tensor core works on the
-// previous chunk (two stages, mbarrier-tracked tcgen05.commit); thread 0
-// issues the MMAs; accumulators live in TMEM and are read back by all warps.
+// One CTA of 16 warps per SM (persistent), warp-specialized: producer warps
+// build the bf16 operand tiles of each K chunk (64 K-elements) in shared
+// memory (128-byte swizzled K-major layout) into a ring of two stages, one
+// thread issues the MMAs and commits each stage back to the producers through
+// an mbarrier, and epilogue warps read a finished accumulator out of TMEM
+// while the tensor core fills the other of two accumulator buffers.
 #include <algorithm>
 
 #include "internal.cuh"
@@ -131,359 +132,461 @@ __device__ __forceinline__ void phases8_axis(const TraceGeo &tr, unsigned k, int
     }
 }
 
-struct TcState {
-    uint32_t tm;            // TMEM base
-    uint32_t mbar[2];
-    uint32_t ncommit[2];
-    bool failed;
+// ------------------------------------------------------ pipeline roles
+// Warp 0 allocates the TMEM (two accumulator buffers of 256 columns) and
+// its lane 0 issues the MMAs; warps 1..11 build the operand tiles into a
+// ring of two shared-memory stages; warps 12..15 (one per TMEM lane quarter)
+// drain a finished accumulator to global memory while the tensor core fills
+// the other.  Four kinds of mbarrier hand the stages and accumulators
+// around:
+//   full[s]   producers -> MMA    (stage s written; one arrival per producer thread)
+//   empty[s]  MMA -> producers    (tcgen05.commit: the MMAs reading stage s are done)
+//   accf[b]   MMA -> epilogue     (tcgen05.commit after an item's last chunk)
+//   acce[b]   epilogue -> MMA     (accumulator b read out; one arrival per epilogue warp)
+// Items are dealt round-robin (item = block + i * grid), so every role walks
+// the same sequence without sharing a counter.  Every wait is bounded; a
+// wait that runs out sets the error flag and the block's abort flag, which
+// ends every role's loop, and the MMA thread waits (bounded) for its last
+// commit before the TMEM is released.
+constexpr int kTcProdWarp0 = 1;
+constexpr int kTcProdWarps = 11;
+constexpr int kTcProdThreads = 32 * kTcProdWarps;
+constexpr int kTcEpiWarp0 = 12;          // warps 12..15: TMEM lane quarters 0..3
+constexpr uint32_t kTcTmemCols = 512;    // two accumulators of 256 columns
+
+struct TcBars {
+    uint64_t full[2], empty[2], accf[2], acce[2];
 };
 
-__device__ __forceinline__ void tc_begin(TcState &s, uint64_t *mbar, uint32_t *tmem_slot) {
+__device__ __forceinline__ void tc_setup(TcBars *bars, uint32_t *tmem_slot, int *abort) {
     const int warp = threadIdx.x >> 5;
-    if (warp == 0) tmem_alloc(smem_u32(tmem_slot), 256);
+    if (warp == 0) tmem_alloc(smem_u32(tmem_slot), kTcTmemCols);
     if (threadIdx.x == 0) {
-        mbar_init(smem_u32(&mbar[0]), 1);
-        mbar_init(smem_u32(&mbar[1]), 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(smem_u32(&bars->full[i]), kTcProdThreads);
+            mbar_init(smem_u32(&bars->empty[i]), 1);
+            mbar_init(smem_u32(&bars->accf[i]), 1);
+            mbar_init(smem_u32(&bars->acce[i]), 4);
+        }
+        *abort = 0;
         mbar_fence_init();
     }
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
-    s.tm = *tmem_slot;
-    s.mbar[0] = smem_u32(&mbar[0]);
-    s.mbar[1] = smem_u32(&mbar[1]);
-    s.ncommit[0] = s.ncommit[1] = 0;
-    s.failed = false;
 }
 
-// wait for the latest commit on buffer b
-__device__ __forceinline__ void tc_wait(TcState &s, int b, int *err, unsigned long long ns) {
-    if (s.ncommit[b] == 0 || s.failed) return;
-    if (!mbar_wait(s.mbar[b], (s.ncommit[b] - 1) & 1u, kTcWait, ns)) {
-        s.failed = true;
-        if ((threadIdx.x & 31) == 0) atomicExch(err, 1);
-    }
+__device__ __forceinline__ void tc_fail(const TcArgs &a, volatile int *abort) {
+    *abort = 1;
+    atomicExch(a.err, 1);
 }
 
-__device__ __forceinline__ void tc_end(TcState &s) {
-    fence_before_sync();
-    __syncthreads();
-    if ((threadIdx.x >> 5) == 0) tmem_dealloc(s.tm, 256);
-}
-
-// Fetch the next work item (uniform); -1 when done or after a timeout.
-__device__ __forceinline__ long long tc_next(const TcArgs &a, TcState &s, long long *slot) {
-    fence_before_sync();
-    if (threadIdx.x == 0) *slot = (long long)atomicAdd(a.counter, 1);
-    const int any_failed = __syncthreads_or(s.failed ? 1 : 0);
-    fence_after_sync();
-    const long long item = *slot;
-    __syncthreads();            // every thread has read the slot before it is rewritten
-    if (any_failed) s.failed = true;
-    if (any_failed || item >= a.total) return -1;
-    return item;
-}
-
-// After a timeout: give the MMAs already issued a bounded chance to finish
-// before the TMEM is released.
-__device__ __forceinline__ void tc_drain(TcState &s, unsigned long long ns) {
-    if (!s.failed) return;
-    for (int b = 0; b < 2; ++b)
-        if (s.ncommit[b] > 0) mbar_wait(s.mbar[b], (s.ncommit[b] - 1) & 1u, kTcWait, ns);
+// wait on barrier `bar` for the phase of the given parity; false on timeout
+// or abort (recording a timeout)
+__device__ __forceinline__ bool tc_wait_bar(const TcArgs &a, uint64_t *bar, uint32_t parity,
+                                            volatile int *abort) {
+    if (*abort) return false;
+    if (mbar_wait_or_abort(smem_u32(bar), parity, kTcWait, a.wait_ns, abort)) return true;
+    tc_fail(a, abort);
+    return false;
 }
 
 // ------------------------------------------------------------- forward
+// Item = (bin k, row tile of <= 128 traces of slice j); K chunks of 32 q
+// samples (64 interleaved bf16 K-elements); accumulator 128 x 4Gp.
 __global__ void __launch_bounds__(kTcThreads, 1)
 slice_fwd_tc_kernel(const TcArgs a, const float2 *__restrict__ X, float2 *__restrict__ Y) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *sm = align1024(smem_raw);
-    __shared__ uint64_t mbar[2];
+    __shared__ TcBars bars;
     __shared__ uint32_t tmem_slot;
-    __shared__ long long s_item;
+    __shared__ int s_abort;
+    volatile int *abort = &s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int Gp = a.Gp, N = 4 * Gp;
     const uint32_t bbytes = (uint32_t)N * 128u;
     const uint32_t stage_bytes = 2 * kTileA + 2 * bbytes;
-    const uint32_t idesc = idesc_bf16_f32(128, N);
     const int nch = (a.nq + 31) >> 5;
     const int J = a.ntheta;
-    TcState s;
-    tc_begin(s, mbar, &tmem_slot);
+    tc_setup(&bars, &tmem_slot, &s_abort);
+    const uint32_t tm = tmem_slot;
 
-    for (;;) {
-        const long long item = tc_next(a, s, &s_item);
-        if (item < 0) break;
-        const int k = (int)(item / a.ntiles);
-        const int4 tile = a.tiles[item - (long long)k * a.ntiles];
-        const int j = tile.x, t0 = tile.y, t1 = tile.z;
-        const int jn = j + 1 == J ? 0 : j + 1;
-        const long long blk = (long long)a.nq * a.G;          // one (bin, slice) block of X
-        const float2 *Xj = X + ((long long)j * a.nbins + k) * blk;
-        const float2 *Xn = X + ((long long)jn * a.nbins + k) * blk;
-
-        for (int c = 0; c < nch; ++c) {
-            const int b = c & 1;
-            if (c >= 2) tc_wait(s, b, a.err, a.wait_ns);
-            unsigned char *ahi = sm + b * stage_bytes, *alo = ahi + kTileA;
-            unsigned char *bhi = alo + kTileA, *blo = bhi + bbytes;
-            // A: E[h][l] for 128 traces x 32 q samples, (Re, Im) interleaved
-            for (int u = tid; u < 128 * 4; u += kTcThreads) {
-                const int r = u >> 2, lb = u & 3;
-                const int t = t0 + r;
-                float2 e[8];
-                if (t < t1) {
-                    const TraceGeo tr = a.geo[t];
-                    if (a.qn)
-                        phases8_axis(tr, (unsigned)k, 32 * c + 8 * lb, a.qn, a.nq, -1.f, 1.f, e);
-                    else
-                        phases8(tr, (unsigned)k, 32 * c + 8 * lb, a.cq, a.nq, -1.f, 1.f, e);
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) e[i] = make_float2(0.f, 0.f);
-                }
-                uint4 h0, l0, h1, l1;
-                split8(reinterpret_cast<const float *>(e), &h0, &l0);
-                split8(reinterpret_cast<const float *>(e) + 8, &h1, &l1);
-                st_chunk(ahi, r, 2 * lb, h0);
-                st_chunk(ahi, r, 2 * lb + 1, h1);
-                st_chunk(alo, r, 2 * lb, l0);
-                st_chunk(alo, r, 2 * lb + 1, l1);
-            }
-            // B: rows (part, slice, g), K = the chunk's q samples
-            for (int u = tid; u < 8 * Gp; u += kTcThreads) {
-                const int g = u % Gp;
-                const int rest = u / Gp;
-                const int sl = rest & 1, lb = rest >> 1;
-                const float2 *Xs = sl ? Xn : Xj;
-                const int l0 = 32 * c + 8 * lb;
-                float vr[16], vi[16];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int l = l0 + i;
-                    float2 x = make_float2(0.f, 0.f);
-                    if (l < a.nq && g < a.G) x = __ldg(Xs + (long long)l * a.G + g);
-                    vr[2 * i] = x.x;
-                    vr[2 * i + 1] = -x.y;
-                    vi[2 * i] = x.y;
-                    vi[2 * i + 1] = x.x;
-                }
-                const int nre = sl * Gp + g, nim = 2 * Gp + sl * Gp + g;
-                uint4 h0, lo0, h1, lo1;
-                split8(vr, &h0, &lo0);
-                split8(vr + 8, &h1, &lo1);
-                st_chunk(bhi, nre, 2 * lb, h0);
-                st_chunk(bhi, nre, 2 * lb + 1, h1);
-                st_chunk(blo, nre, 2 * lb, lo0);
-                st_chunk(blo, nre, 2 * lb + 1, lo1);
-                split8(vi, &h0, &lo0);
-                split8(vi + 8, &h1, &lo1);
-                st_chunk(bhi, nim, 2 * lb, h0);
-                st_chunk(bhi, nim, 2 * lb + 1, h1);
-                st_chunk(blo, nim, 2 * lb, lo0);
-                st_chunk(blo, nim, 2 * lb + 1, lo1);
-            }
-            fence_async_smem();
-            __syncthreads();
-            if (tid == 0 && !a.stall) {
+    if (warp == 0) {
+        // ---------------------------------------------------------- MMA
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16_f32(128, N);
+            uint32_t cc = 0, last_bar = 0, last_par = 0;
+            bool issued = false;
+            int it = 0;
+            for (long long item = blockIdx.x; item < a.total; item += gridDim.x, ++it) {
+                const int ab = it & 1;
+                if (!tc_wait_bar(a, &bars.acce[ab], ((it >> 1) & 1) ^ 1, abort)) break;
                 fence_after_sync();
-                const uint32_t a_hi = smem_u32(ahi), a_lo = smem_u32(alo);
-                const uint32_t b_hi = smem_u32(bhi), b_lo = smem_u32(blo);
+                const uint32_t d = tm + (uint32_t)(ab * N);
+                bool ok = true;
+                for (int c = 0; c < nch; ++c, ++cc) {
+                    const int st = cc & 1;
+                    if (!tc_wait_bar(a, &bars.full[st], (cc >> 1) & 1, abort)) { ok = false; break; }
+                    fence_after_sync();
+                    if (!a.stall) {
+                        unsigned char *ahi = sm + st * stage_bytes, *alo = ahi + kTileA;
+                        unsigned char *bhi = alo + kTileA, *blo = bhi + bbytes;
+                        const uint32_t a_hi = smem_u32(ahi), a_lo = smem_u32(alo);
+                        const uint32_t b_hi = smem_u32(bhi), b_lo = smem_u32(blo);
 #pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    mma_bf16(s.tm, sw128_desc(a_hi + 32 * t), sw128_desc(b_hi + 32 * t), idesc,
-                             (c > 0 || t > 0) ? 1u : 0u);
-                    mma_bf16(s.tm, sw128_desc(a_hi + 32 * t), sw128_desc(b_lo + 32 * t), idesc, 1u);
-                    mma_bf16(s.tm, sw128_desc(a_lo + 32 * t), sw128_desc(b_hi + 32 * t), idesc, 1u);
+                        for (int t = 0; t < 4; ++t) {
+                            mma_bf16(d, sw128_desc(a_hi + 32 * t), sw128_desc(b_hi + 32 * t),
+                                     idesc, (c > 0 || t > 0) ? 1u : 0u);
+                            mma_bf16(d, sw128_desc(a_hi + 32 * t), sw128_desc(b_lo + 32 * t),
+                                     idesc, 1u);
+                            mma_bf16(d, sw128_desc(a_lo + 32 * t), sw128_desc(b_hi + 32 * t),
+                                     idesc, 1u);
+                        }
+                        mma_commit(smem_u32(&bars.empty[st]));
+                        issued = true;
+                        last_bar = smem_u32(&bars.empty[st]);
+                        last_par = (cc >> 1) & 1;
+                    }
                 }
-                mma_commit(s.mbar[b]);
+                if (!ok) break;
+                if (!a.stall) {
+                    mma_commit(smem_u32(&bars.accf[ab]));
+                    last_bar = smem_u32(&bars.accf[ab]);
+                    last_par = (it >> 1) & 1;
+                }
             }
-            s.ncommit[b]++;
+            // the TMEM is released only after the MMAs issued have finished
+            if (issued) mbar_wait(last_bar, last_par, kTcWait, a.wait_ns);
         }
-        tc_wait(s, (nch - 1) & 1, a.err, a.wait_ns);
-        fence_after_sync();
-        if (s.failed) continue;
-
-        // epilogue: Y[h][g] = scale (w0 P[h][g, j] + w1 P[h][g, j+1])
-        const int q = warp & 3, quarter = warp >> 2;
-        const int r = 32 * q + lane;
-        const int t = t0 + r;
-        const bool valid = t < t1;
-        TraceGeo tr{};
-        if (valid) tr = a.geo[t];
-        const uint32_t lanebase = s.tm + ((uint32_t)(32 * q) << 16);
-        const int s0 = a.ss[j], cnt = a.ss[j + 1] - s0;
-        float2 *Yrow = Y + ((long long)a.nbins * s0 + (long long)k * cnt + (valid ? t - s0 : 0)) * a.G;
-        for (int gb = 16 * quarter; gb < Gp; gb += 64) {
-            float re0[16], re1[16], im0[16], im1[16];
-            tmem_ld16(lanebase + gb, re0);
-            tmem_ld16(lanebase + Gp + gb, re1);
-            tmem_ld16(lanebase + 2 * Gp + gb, im0);
-            tmem_ld16(lanebase + 3 * Gp + gb, im1);
-            if (valid) {
-                const float w0 = a.scale * tr.w0, w1 = a.scale * tr.w1;
+    } else if (warp < kTcEpiWarp0) {
+        // ---------------------------------------------------- producers
+        const int pid = tid - 32 * kTcProdWarp0;
+        uint32_t cc = 0;
+        for (long long item = blockIdx.x; item < a.total && !*abort; item += gridDim.x) {
+            const int k = (int)(item / a.ntiles);
+            const int4 tile = a.tiles[item - (long long)k * a.ntiles];
+            const int j = tile.x, t0 = tile.y, t1 = tile.z;
+            const int jn = j + 1 == J ? 0 : j + 1;
+            const long long blk = (long long)a.nq * a.G;      // one (bin, slice) block of X
+            const float2 *Xj = X + ((long long)j * a.nbins + k) * blk;
+            const float2 *Xn = X + ((long long)jn * a.nbins + k) * blk;
+            for (int c = 0; c < nch; ++c, ++cc) {
+                const int st = cc & 1;
+                if (!tc_wait_bar(a, &bars.empty[st], ((cc >> 1) & 1) ^ 1, abort)) break;
+                unsigned char *ahi = sm + st * stage_bytes, *alo = ahi + kTileA;
+                unsigned char *bhi = alo + kTileA, *blo = bhi + bbytes;
+                for (int u = pid; u < 128 * 4 + 8 * Gp; u += kTcProdThreads) {
+                    if (u < 128 * 4) {
+                        // A: E[h][l] for 128 traces x 32 q samples, (Re, Im) interleaved
+                        const int r = u >> 2, lb = u & 3;
+                        const int t = t0 + r;
+                        float2 e[8];
+                        if (t < t1) {
+                            const TraceGeo tr = a.geo[t];
+                            if (a.qn)
+                                phases8_axis(tr, (unsigned)k, 32 * c + 8 * lb, a.qn, a.nq, -1.f,
+                                             1.f, e);
+                            else
+                                phases8(tr, (unsigned)k, 32 * c + 8 * lb, a.cq, a.nq, -1.f, 1.f,
+                                        e);
+                        } else {
 #pragma unroll
-                for (int i = 0; i < 16; ++i)
-                    if (gb + i < a.G)
-                        Yrow[gb + i] = make_float2(fmaf(w0, re0[i], w1 * re1[i]),
-                                                   fmaf(w0, im0[i], w1 * im1[i]));
+                            for (int i = 0; i < 8; ++i) e[i] = make_float2(0.f, 0.f);
+                        }
+                        uint4 h0, l0, h1, l1;
+                        split8(reinterpret_cast<const float *>(e), &h0, &l0);
+                        split8(reinterpret_cast<const float *>(e) + 8, &h1, &l1);
+                        st_chunk(ahi, r, 2 * lb, h0);
+                        st_chunk(ahi, r, 2 * lb + 1, h1);
+                        st_chunk(alo, r, 2 * lb, l0);
+                        st_chunk(alo, r, 2 * lb + 1, l1);
+                    } else {
+                        // B: rows (part, slice, g), K = the chunk's q samples
+                        const int v = u - 128 * 4;
+                        const int g = v % Gp;
+                        const int rest = v / Gp;
+                        const int sl = rest & 1, lb = rest >> 1;
+                        const float2 *Xs = sl ? Xn : Xj;
+                        const int l0 = 32 * c + 8 * lb;
+                        float vr[16], vi[16];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const int l = l0 + i;
+                            float2 x = make_float2(0.f, 0.f);
+                            if (l < a.nq && g < a.G) x = __ldg(Xs + (long long)l * a.G + g);
+                            vr[2 * i] = x.x;
+                            vr[2 * i + 1] = -x.y;
+                            vi[2 * i] = x.y;
+                            vi[2 * i + 1] = x.x;
+                        }
+                        const int nre = sl * Gp + g, nim = 2 * Gp + sl * Gp + g;
+                        uint4 h0, lo0, h1, lo1;
+                        split8(vr, &h0, &lo0);
+                        split8(vr + 8, &h1, &lo1);
+                        st_chunk(bhi, nre, 2 * lb, h0);
+                        st_chunk(bhi, nre, 2 * lb + 1, h1);
+                        st_chunk(blo, nre, 2 * lb, lo0);
+                        st_chunk(blo, nre, 2 * lb + 1, lo1);
+                        split8(vi, &h0, &lo0);
+                        split8(vi + 8, &h1, &lo1);
+                        st_chunk(bhi, nim, 2 * lb, h0);
+                        st_chunk(bhi, nim, 2 * lb + 1, h1);
+                        st_chunk(blo, nim, 2 * lb, lo0);
+                        st_chunk(blo, nim, 2 * lb + 1, lo1);
+                    }
+                }
+                fence_async_smem();     // this thread's tile writes -> the tensor core
+                mbar_arrive(smem_u32(&bars.full[st]));
             }
+        }
+    } else {
+        // ----------------------------------------------------- epilogue
+        // Y[h][g] = scale (w0 P[h][g, j] + w1 P[h][g, j+1])
+        const int q = warp & 3;
+        int it = 0;
+        for (long long item = blockIdx.x; item < a.total; item += gridDim.x, ++it) {
+            const int ab = it & 1;
+            if (!tc_wait_bar(a, &bars.accf[ab], (it >> 1) & 1, abort)) break;
+            fence_after_sync();
+            const int k = (int)(item / a.ntiles);
+            const int4 tile = a.tiles[item - (long long)k * a.ntiles];
+            const int j = tile.x, t0 = tile.y, t1 = tile.z;
+            const int r = 32 * q + lane;
+            const int t = t0 + r;
+            const bool valid = t < t1;
+            TraceGeo tr{};
+            if (valid) tr = a.geo[t];
+            const uint32_t lanebase = tm + ((uint32_t)(32 * q) << 16) + (uint32_t)(ab * N);
+            const int s0 = a.ss[j], cnt = a.ss[j + 1] - s0;
+            float2 *Yrow =
+                Y + ((long long)a.nbins * s0 + (long long)k * cnt + (valid ? t - s0 : 0)) * a.G;
+            const float w0 = a.scale * tr.w0, w1 = a.scale * tr.w1;
+            for (int gb = 0; gb < Gp; gb += 16) {
+                float re0[16], re1[16], im0[16], im1[16];
+                tmem_ld16(lanebase + gb, re0);
+                tmem_ld16(lanebase + Gp + gb, re1);
+                tmem_ld16(lanebase + 2 * Gp + gb, im0);
+                tmem_ld16(lanebase + 3 * Gp + gb, im1);
+                if (valid) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        if (gb + i < a.G)
+                            Yrow[gb + i] = make_float2(fmaf(w0, re0[i], w1 * re1[i]),
+                                                       fmaf(w0, im0[i], w1 * im1[i]));
+                }
+            }
+            fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&bars.acce[ab]));
         }
     }
-    tc_drain(s, a.wait_ns);
-    tc_end(s);
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tm, kTcTmemCols);
 }
 
 // ------------------------------------------------------------- adjoint
+// Item = (bin k, slice j); M = q (nmt tiles of 128), K = the traces of
+// slices j (weight w0) and j - 1 (weight w1) in chunks of 32; accumulator
+// nmt x (128 x 2Gp).
 __global__ void __launch_bounds__(kTcThreads, 1)
 slice_adj_tc_kernel(const TcArgs a, const float2 *__restrict__ Yh, float2 *__restrict__ Xh) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *sm = align1024(smem_raw);
-    __shared__ uint64_t mbar[2];
+    __shared__ TcBars bars;
     __shared__ uint32_t tmem_slot;
-    __shared__ long long s_item;
+    __shared__ int s_abort;
+    volatile int *abort = &s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int Gp = a.Gp, N = 2 * Gp;
     const uint32_t bbytes = (uint32_t)N * 128u;
     const uint32_t stage_bytes = 4 * kTileA + 2 * bbytes;
-    const uint32_t idesc = idesc_bf16_f32(128, N);
     const int nmt = a.nq > 128 ? 2 : 1;
     const int J = a.ntheta;
-    TcState s;
-    tc_begin(s, mbar, &tmem_slot);
+    const int acc_cols = 2 * N;          // columns per accumulator buffer (room for two M tiles)
+    tc_setup(&bars, &tmem_slot, &s_abort);
+    const uint32_t tm = tmem_slot;
 
-    for (;;) {
-        const long long item = tc_next(a, s, &s_item);
-        if (item < 0) break;
-        const int k = (int)(item / J);
-        const int j = (int)(item - (long long)k * J);
-        const int jm = j == 0 ? J - 1 : j - 1;
-        const int a0 = a.ss[j], n1 = a.ss[j + 1] - a0;      // weight w0
-        const int b0 = a.ss[jm], n2 = a.ss[jm + 1] - b0;    // weight w1
-        const int ntot = n1 + n2;
-        const int nch = (ntot + 31) >> 5;
-        // slice blocks of Y^: slice j (weight w0) and slice j - 1 (weight w1)
-        const float2 *Ya = Yh + ((long long)a.nbins * a0 + (long long)k * n1) * a.G;
-        const float2 *Yb = Yh + ((long long)a.nbins * b0 + (long long)k * n2) * a.G;
-
-        for (int c = 0; c < nch; ++c) {
-            const int b = c & 1;
-            if (c >= 2) tc_wait(s, b, a.err, a.wait_ns);
-            unsigned char *st0 = sm + b * stage_bytes;
-            unsigned char *bhi = st0 + 4 * kTileA, *blo = bhi + bbytes;
-            // A: w conj(E)[l][h], rows l (two M-tiles), K = 32 traces
-            {
-                const int hh = lane;
-                const int p = 32 * c + hh;
-                TraceGeo tr{};
-                float wgt = 0.f;
-                const bool have = p < ntot;
-                if (have) {
-                    tr = a.geo[p < n1 ? a0 + p : b0 + (p - n1)];
-                    wgt = p < n1 ? tr.w0 : tr.w1;
+    if (warp == 0) {
+        // ---------------------------------------------------------- MMA
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16_f32(128, N);
+            uint32_t cc = 0, last_bar = 0, last_par = 0;
+            bool issued = false;
+            int it = 0;
+            for (long long item = blockIdx.x; item < a.total; item += gridDim.x, ++it) {
+                const int ab = it & 1;
+                const int k = (int)(item / J);
+                const int j = (int)(item - (long long)k * J);
+                const int jm = j == 0 ? J - 1 : j - 1;
+                const int ntot = (a.ss[j + 1] - a.ss[j]) + (a.ss[jm + 1] - a.ss[jm]);
+                const int nch = (ntot + 31) >> 5;
+                if (!tc_wait_bar(a, &bars.acce[ab], ((it >> 1) & 1) ^ 1, abort)) break;
+                fence_after_sync();
+                bool ok = true;
+                for (int c = 0; c < nch; ++c, ++cc) {
+                    const int st = cc & 1;
+                    if (!tc_wait_bar(a, &bars.full[st], (cc >> 1) & 1, abort)) { ok = false; break; }
+                    fence_after_sync();
+                    if (!a.stall) {
+                        unsigned char *st0 = sm + st * stage_bytes;
+                        const uint32_t b_hi = smem_u32(st0 + 4 * kTileA);
+                        const uint32_t b_lo = b_hi + bbytes;
+                        for (int mt = 0; mt < nmt; ++mt) {
+                            const uint32_t a_hi = smem_u32(st0 + (2 * mt) * kTileA);
+                            const uint32_t a_lo = a_hi + kTileA;
+                            const uint32_t d = tm + (uint32_t)(ab * acc_cols + mt * N);
+#pragma unroll
+                            for (int t = 0; t < 4; ++t) {
+                                mma_bf16(d, sw128_desc(a_hi + 32 * t), sw128_desc(b_hi + 32 * t),
+                                         idesc, (c > 0 || t > 0) ? 1u : 0u);
+                                mma_bf16(d, sw128_desc(a_hi + 32 * t), sw128_desc(b_lo + 32 * t),
+                                         idesc, 1u);
+                                mma_bf16(d, sw128_desc(a_lo + 32 * t), sw128_desc(b_hi + 32 * t),
+                                         idesc, 1u);
+                            }
+                        }
+                        mma_commit(smem_u32(&bars.empty[st]));
+                        issued = true;
+                        last_bar = smem_u32(&bars.empty[st]);
+                        last_par = (cc >> 1) & 1;
+                    }
                 }
-                for (int lb = warp; lb < 16 * nmt; lb += kTcThreads / 32) {
-                    const int l0 = 8 * lb;
-                    const int mt = l0 >> 7;
-                    unsigned char *ahi = st0 + (2 * mt) * kTileA, *alo = ahi + kTileA;
-                    float2 e[8];
-                    if (have) {
-                        if (a.qn)
-                            phases8_axis(tr, (unsigned)k, l0, a.qn, a.nq, 1.f, wgt, e);
-                        else
-                            phases8(tr, (unsigned)k, l0, a.cq, a.nq, 1.f, wgt, e);
+                if (!ok) break;
+                if (!a.stall) {
+                    // with no chunk (no traces) the commit arrives at once
+                    mma_commit(smem_u32(&bars.accf[ab]));
+                    issued = true;
+                    last_bar = smem_u32(&bars.accf[ab]);
+                    last_par = (it >> 1) & 1;
+                }
+            }
+            if (issued) mbar_wait(last_bar, last_par, kTcWait, a.wait_ns);
+        }
+    } else if (warp < kTcEpiWarp0) {
+        // ---------------------------------------------------- producers
+        const int pid = tid - 32 * kTcProdWarp0;
+        uint32_t cc = 0;
+        for (long long item = blockIdx.x; item < a.total && !*abort; item += gridDim.x) {
+            const int k = (int)(item / J);
+            const int j = (int)(item - (long long)k * J);
+            const int jm = j == 0 ? J - 1 : j - 1;
+            const int a0 = a.ss[j], n1 = a.ss[j + 1] - a0;      // weight w0
+            const int b0 = a.ss[jm], n2 = a.ss[jm + 1] - b0;    // weight w1
+            const int ntot = n1 + n2;
+            const int nch = (ntot + 31) >> 5;
+            const float2 *Ya = Yh + ((long long)a.nbins * a0 + (long long)k * n1) * a.G;
+            const float2 *Yb = Yh + ((long long)a.nbins * b0 + (long long)k * n2) * a.G;
+            const int na = 32 * 16 * nmt;    // A units: (trace, 8-q group)
+            for (int c = 0; c < nch; ++c, ++cc) {
+                const int st = cc & 1;
+                if (!tc_wait_bar(a, &bars.empty[st], ((cc >> 1) & 1) ^ 1, abort)) break;
+                unsigned char *st0 = sm + st * stage_bytes;
+                unsigned char *bhi = st0 + 4 * kTileA, *blo = bhi + bbytes;
+                for (int u = pid; u < na + 8 * Gp; u += kTcProdThreads) {
+                    if (u < na) {
+                        // A: w conj(E)[l][h], rows l (M tiles), K = 32 traces
+                        const int hh = u & 31, lb = u >> 5;
+                        const int p = 32 * c + hh;
+                        const int l0 = 8 * lb;
+                        const int mt = l0 >> 7;
+                        unsigned char *ahi = st0 + (2 * mt) * kTileA, *alo = ahi + kTileA;
+                        float2 e[8];
+                        if (p < ntot) {
+                            const TraceGeo tr = a.geo[p < n1 ? a0 + p : b0 + (p - n1)];
+                            const float wgt = p < n1 ? tr.w0 : tr.w1;
+                            if (a.qn)
+                                phases8_axis(tr, (unsigned)k, l0, a.qn, a.nq, 1.f, wgt, e);
+                            else
+                                phases8(tr, (unsigned)k, l0, a.cq, a.nq, 1.f, wgt, e);
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) e[i] = make_float2(0.f, 0.f);
+                        }
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const int r = (l0 & 127) + i;
+                            uint32_t h, lo;
+                            split2(e[i].x, e[i].y, &h, &lo);
+                            const uint32_t off = sw128_offset((uint32_t)r, (uint32_t)(2 * hh));
+                            *reinterpret_cast<uint32_t *>(ahi + off) = h;
+                            *reinterpret_cast<uint32_t *>(alo + off) = lo;
+                        }
+                    } else {
+                        // B: rows (part, g), K = 32 traces x (Re, Im); one unit is
+                        // one 16-byte chunk (4 traces) of a row pair
+                        const int v = u - na;
+                        const int g = v % Gp, tq = v / Gp;
+                        float vr[8], vi[8];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const int p = 32 * c + 4 * tq + i;
+                            float2 y = make_float2(0.f, 0.f);
+                            if (p < ntot && g < a.G)
+                                y = __ldg(p < n1 ? Ya + (long long)p * a.G + g
+                                                 : Yb + (long long)(p - n1) * a.G + g);
+                            vr[2 * i] = y.x;
+                            vr[2 * i + 1] = -y.y;
+                            vi[2 * i] = y.y;
+                            vi[2 * i + 1] = y.x;
+                        }
+                        uint4 h, lo;
+                        split8(vr, &h, &lo);
+                        st_chunk(bhi, g, tq, h);
+                        st_chunk(blo, g, tq, lo);
+                        split8(vi, &h, &lo);
+                        st_chunk(bhi, Gp + g, tq, h);
+                        st_chunk(blo, Gp + g, tq, lo);
+                    }
+                }
+                fence_async_smem();
+                mbar_arrive(smem_u32(&bars.full[st]));
+            }
+        }
+    } else {
+        // ----------------------------------------------------- epilogue
+        // X^[l][j][g] = scale * accumulator (zero without traces)
+        const int q = warp & 3;
+        int it = 0;
+        for (long long item = blockIdx.x; item < a.total; item += gridDim.x, ++it) {
+            const int ab = it & 1;
+            if (!tc_wait_bar(a, &bars.accf[ab], (it >> 1) & 1, abort)) break;
+            fence_after_sync();
+            const int k = (int)(item / J);
+            const int j = (int)(item - (long long)k * J);
+            const int jm = j == 0 ? J - 1 : j - 1;
+            const int ntot = (a.ss[j + 1] - a.ss[j]) + (a.ss[jm + 1] - a.ss[jm]);
+            for (int mt = 0; mt < nmt; ++mt) {
+                const int l = 128 * mt + 32 * q + lane;
+                const uint32_t base = tm + ((uint32_t)(32 * q) << 16) +
+                                      (uint32_t)(ab * acc_cols + mt * N);
+                float2 *Xrow =
+                    Xh + (((long long)j * a.nbins + k) * a.nq + (l < a.nq ? l : 0)) * a.G;
+                for (int gb = 0; gb < Gp; gb += 16) {
+                    float re[16], im[16];
+                    if (ntot > 0) {
+                        tmem_ld16(base + gb, re);
+                        tmem_ld16(base + Gp + gb, im);
                     } else {
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) e[i] = make_float2(0.f, 0.f);
+                        for (int i = 0; i < 16; ++i) re[i] = im[i] = 0.f;
                     }
+                    if (l < a.nq) {
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const int r = (l0 & 127) + i;
-                        uint32_t h, lo;
-                        split2(e[i].x, e[i].y, &h, &lo);
-                        const uint32_t off = sw128_offset((uint32_t)r, (uint32_t)(2 * hh));
-                        *reinterpret_cast<uint32_t *>(ahi + off) = h;
-                        *reinterpret_cast<uint32_t *>(alo + off) = lo;
+                        for (int i = 0; i < 16; ++i)
+                            if (gb + i < a.G)
+                                Xrow[gb + i] = make_float2(a.scale * re[i], a.scale * im[i]);
                     }
                 }
             }
-            // B: rows (part, g), K = 32 traces x (Re, Im); one unit is one
-            // 16-byte chunk (4 traces) of a row pair, so 8 Gp units
-            for (int u = tid; u < 8 * Gp; u += kTcThreads) {
-                const int g = u % Gp, tq = u / Gp;
-                float vr[8], vi[8];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int p = 32 * c + 4 * tq + i;
-                    float2 y = make_float2(0.f, 0.f);
-                    if (p < ntot && g < a.G)
-                        y = __ldg(p < n1 ? Ya + (long long)p * a.G + g
-                                         : Yb + (long long)(p - n1) * a.G + g);
-                    vr[2 * i] = y.x;
-                    vr[2 * i + 1] = -y.y;
-                    vi[2 * i] = y.y;
-                    vi[2 * i + 1] = y.x;
-                }
-                uint4 h, lo;
-                split8(vr, &h, &lo);
-                st_chunk(bhi, g, tq, h);
-                st_chunk(blo, g, tq, lo);
-                split8(vi, &h, &lo);
-                st_chunk(bhi, Gp + g, tq, h);
-                st_chunk(blo, Gp + g, tq, lo);
-            }
-            fence_async_smem();
-            __syncthreads();
-            if (tid == 0 && !a.stall) {
-                fence_after_sync();
-                const uint32_t b_hi = smem_u32(bhi), b_lo = smem_u32(blo);
-                for (int mt = 0; mt < nmt; ++mt) {
-                    const uint32_t a_hi = smem_u32(st0 + (2 * mt) * kTileA);
-                    const uint32_t a_lo = a_hi + kTileA;
-                    const uint32_t d = s.tm + (uint32_t)(mt * N);
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        mma_bf16(d, sw128_desc(a_hi + 32 * t), sw128_desc(b_hi + 32 * t), idesc,
-                                 (c > 0 || t > 0) ? 1u : 0u);
-                        mma_bf16(d, sw128_desc(a_hi + 32 * t), sw128_desc(b_lo + 32 * t), idesc,
-                                 1u);
-                        mma_bf16(d, sw128_desc(a_lo + 32 * t), sw128_desc(b_hi + 32 * t), idesc,
-                                 1u);
-                    }
-                }
-                mma_commit(s.mbar[b]);
-            }
-            s.ncommit[b]++;
-        }
-        if (nch > 0) tc_wait(s, (nch - 1) & 1, a.err, a.wait_ns);
-        fence_after_sync();
-        if (s.failed) continue;
-
-        // epilogue: X^[l][j][g] = scale * accumulator (zero without traces)
-        const int q = warp & 3, mt = (warp >> 2) & 1, half = warp >> 3;
-        if (mt < nmt) {
-            const int l = 128 * mt + 32 * q + lane;
-            const uint32_t base = s.tm + ((uint32_t)(32 * q) << 16) + (uint32_t)(mt * N);
-            float2 *Xrow = Xh + (((long long)j * a.nbins + k) * a.nq + (l < a.nq ? l : 0)) * a.G;
-            for (int gb = 16 * half; gb < Gp; gb += 32) {
-                float re[16], im[16];
-                if (nch > 0) {
-                    tmem_ld16(base + gb, re);
-                    tmem_ld16(base + Gp + gb, im);
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) re[i] = im[i] = 0.f;
-                }
-                if (l < a.nq) {
-#pragma unroll
-                    for (int i = 0; i < 16; ++i)
-                        if (gb + i < a.G)
-                            Xrow[gb + i] = make_float2(a.scale * re[i], a.scale * im[i]);
-                }
-            }
+            fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&bars.acce[ab]));
         }
     }
-    tc_drain(s, a.wait_ns);
-    tc_end(s);
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tm, kTcTmemCols);
 }
 
 // ------------------------------------------------------------- host side

@@ -126,5 +126,30 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32
     return false;
 }
 
+// arrive (release, CTA scope) on an mbarrier
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(mbar) : "memory");
+}
+
+// mbar_wait that also gives up (false) as soon as *abort is set by another
+// thread of the block (checked every 64 polls)
+__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t mbar, uint32_t parity,
+                                                   uint32_t limit,
+                                                   unsigned long long timeout_ns,
+                                                   const volatile int *abort) {
+    const unsigned long long t0 = globaltimer_ns();
+    for (uint32_t i = 0; i < limit; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+        if (done) return true;
+        if ((i & 63u) == 63u && (*abort || globaltimer_ns() - t0 > timeout_ns)) return false;
+    }
+    return false;
+}
+
 }  // namespace tc
 }  // namespace aahrt

@@ -40,6 +40,14 @@ __device__ __forceinline__ RowRange load_rng(const RowRange *p) {
 
 constexpr int kPackBatch = 8;   // spectrum loads in flight per thread (c2r pack)
 
+// Threads of a time-kernel block: 256 while two blocks fit in one SM's shared
+// memory, else 512 (one block per SM, e.g. the 8192-point frames of long
+// traces), so an SM keeps 16 warps in flight either way.  Both run under the
+// same 128-register cap.
+static int time_threads(size_t smem) {
+    return smem + 512 <= (size_t)kTimeSmemTwoBlocks ? kThreadsTime : kMaxThreadsTime;
+}
+
 // Asynchronous global -> shared copies (no registers held while in flight).
 template <int BYTES>
 __device__ __forceinline__ void cp_async(void *smem, const void *gmem) {
@@ -205,7 +213,7 @@ __device__ __forceinline__ void r2c_core(float2 *sm, const float *stg, const flo
 }
 
 template <int LP, int INTERP, bool TRANS>
-__global__ void __launch_bounds__(kThreadsTime, 2)
+__global__ void __launch_bounds__(kMaxThreadsTime, 1)
 r2c_kernel(const float *__restrict__ in, float2 *__restrict__ out,
            const ColGroup *__restrict__ groups, DevResampler rs, int nrow_in,
            const float2 *__restrict__ tw, int L, int nbins, YBound ybd) {
@@ -407,7 +415,7 @@ __device__ __forceinline__ void c2r_core(float2 *sm, float *sfr, const float2 *_
 }
 
 template <int LP, int INTERP, bool TRANS, int EPI>
-__global__ void __launch_bounds__(kThreadsTime, 2)
+__global__ void __launch_bounds__(kMaxThreadsTime, 1)
 c2r_kernel(const float2 *__restrict__ in, float *__restrict__ out,
            const float *__restrict__ aux, FistaArgs fa,
            const ColGroup *__restrict__ groups, DevResampler rs, int n_in,
@@ -430,7 +438,7 @@ c2r_kernel(const float2 *__restrict__ in, float *__restrict__ out,
 // (the next iteration's first stage).  The spectrum is read and rewritten in
 // place: a block touches only its own columns.
 template <int LP, int INTERP, bool SYN_TRANS, int EPI>
-__global__ void __launch_bounds__(kThreadsTime, 2)
+__global__ void __launch_bounds__(kMaxThreadsTime, 1)
 c2r_r2c_kernel(float2 *spec, const float *__restrict__ aux, FistaArgs fa,
                const ColGroup *__restrict__ groups, DevResampler rs_syn, int n_in,
                DevResampler rs_ana, int nrow_mid, const float2 *__restrict__ tw, int L,
@@ -465,10 +473,10 @@ static void r2c_launch(bool model_side, int grid, size_t smem, cudaStream_t st, 
                        float2 *out, const ColGroup *cg, DevResampler rs, int nrow_in,
                        const float2 *tw, int L, int nbins, YBound ybd = YBound{}) {
     if (model_side)
-        r2c_kernel<LP, INTERP, false><<<grid, kThreadsTime, smem, st>>>(in, out, cg, rs, nrow_in,
+        r2c_kernel<LP, INTERP, false><<<grid, time_threads(smem), smem, st>>>(in, out, cg, rs, nrow_in,
                                                                         tw, L, nbins, YBound{});
     else
-        r2c_kernel<LP, INTERP, true><<<grid, kThreadsTime, smem, st>>>(in, out, cg, rs, nrow_in,
+        r2c_kernel<LP, INTERP, true><<<grid, time_threads(smem), smem, st>>>(in, out, cg, rs, nrow_in,
                                                                        tw, L, nbins, ybd);
 }
 
@@ -486,10 +494,10 @@ static void c2r_launch(bool model_side, int grid, size_t smem, cudaStream_t st,
                        const ColGroup *cg, DevResampler rs, int n_in, const float2 *tw, int L,
                        int nbins) {
     if (model_side)
-        c2r_kernel<LP, INTERP, true, EPI><<<grid, kThreadsTime, smem, st>>>(
+        c2r_kernel<LP, INTERP, true, EPI><<<grid, time_threads(smem), smem, st>>>(
             in, out, aux, fa, cg, rs, n_in, tw, L, nbins);
     else
-        c2r_kernel<LP, INTERP, false, EPI><<<grid, kThreadsTime, smem, st>>>(
+        c2r_kernel<LP, INTERP, false, EPI><<<grid, time_threads(smem), smem, st>>>(
             in, out, aux, fa, cg, rs, n_in, tw, L, nbins);
 }
 
@@ -586,12 +594,14 @@ cudaError_t launch_c2r_r2c(Plan &p, bool model_side, float2 *spec, const float *
     prof_begin(p, stage, st);
     if (model_side) {
         AAHRT_LP_SWITCH(p.lp, AAHRT_INTERP_SWITCH(p.interp, (
-            c2r_r2c_kernel<LPc, IPc, true, EPI_FISTA><<<n, kThreadsTime, p.smem_fused_model, st>>>(
+            c2r_r2c_kernel<LPc, IPc, true, EPI_FISTA><<<n, time_threads(p.smem_fused_model),
+                                                         p.smem_fused_model, st>>>(
                 spec, nullptr, fa, cg, p.ST, p.ns, p.S, p.ntau, p.tw_t, p.L, p.nbins,
                 YBound{}))));
     } else {
         AAHRT_LP_SWITCH(p.lp, AAHRT_INTERP_SWITCH(p.interp, (
-            c2r_r2c_kernel<LPc, IPc, false, EPI_RESIDUAL><<<n, kThreadsTime, p.smem_r2c_data,
+            c2r_r2c_kernel<LPc, IPc, false, EPI_RESIDUAL><<<n, time_threads(p.smem_r2c_data),
+                                                           p.smem_r2c_data,
                                                            st>>>(
                 spec, aux, FistaArgs{}, cg, p.U, p.ns, p.UT, p.nt, p.tw_t, p.L, p.nbins, yb))));
     }
