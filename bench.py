@@ -498,7 +498,9 @@ def measure(kind, args, rank, world, dev):
     if world == 1 and not args.no_cpu_baseline:
         if batch:
             line["cpu_baseline"], line["err_vs_fp64"] = cpu_baseline_batch(cubes, gp, d, dev)
-            line["err_vs_fp64"]["fista"] = fista_error_batch(cubes, gp, d, dev, cg, cl)
+            fe, mo = fista_error_batch(cubes, gp, d, dev, cg, cl)
+            line["err_vs_fp64"]["fista"] = fe
+            line["per_cube_fp32"] = per_cube_arm(cubes, info, cg, cl, fe, mo, dev, value)
         else:
             line["cpu_baseline"], line["err_vs_fp64"] = cpu_baseline(g, gp, d, dev, q_axis=qa,
                                                                      kind=kind)
@@ -671,7 +673,67 @@ def fista_error_batch(cubes, gp, d_dev, dev, cg, cl):
     mg = m[i * msz:(i + 1) * msz].cpu().numpy().astype(np.float64).reshape(mo.shape)
     return {"cube": i, "fold": int(folds[i]), "iters": BATCH_ITERS,
             "rel_l2": float(np.linalg.norm(mg - mo) / np.linalg.norm(mo)),
-            "oracle_seconds": round(el, 1)}
+            "gamma": gamma, "lambda": lam, "oracle_seconds": round(el, 1)}, mo
+
+
+def per_cube_arm(cubes, info, cg, cl, fe, mo, dev, batched_value, nsample=16):
+    """The plain per-cube form of the same work: one single-cube FP32 plan
+    per cube (the batch plan's spreading width, azimuth group and column
+    pairs), each cube's 50-iteration FISTA solve run on its own, one cube
+    after another; nsample cubes spread evenly over the fold range.  Returns
+    its rate in cube-pairs/s beside the batched plan's, and the FISTA output
+    error against the FP64 checker on the smallest-fold cube (solved with the
+    checker's step and threshold, as in err_vs_fp64.fista)."""
+    import numpy as np
+    import torch
+
+    from paper_2505_00387_gb300.plan import AahrtPlan
+
+    folds = np.array([c.ntr for c in cubes])
+    picks = fold_picks(folds, nsample)
+    r2max = max(float(np.max(x.hx ** 2 + x.hy ** 2)) for x in cubes)
+    runs = []
+    for i in picks:
+        c = cubes[i]
+        # the batch's time plan (r2max): the same operator as the batched plan
+        p = AahrtPlan(**c.geom_kwargs(), spread_width=info.spread_width,
+                      theta_group=info.theta_group, time_pairs=info.time_pairs, r2max=r2max)
+        d = torch.from_numpy(c.d.astype(np.float32).ravel()).to(dev)
+        m = torch.zeros(p.model_len, device=dev)
+        g, lam = (fe["gamma"], fe["lambda"]) if i == fe["cube"] else (float(cg[i]), float(cl[i]))
+        runs.append((i, p, d, m, g, lam))
+
+    def one_pass():
+        for _, p, d, m, g, lam in runs:
+            p.sparse_solve(d, lam, BATCH_ITERS, m, gamma=g, use_graph=True, want_info=False)
+
+    one_pass()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 2
+    e0.record()
+    for _ in range(reps):
+        one_pass()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    rate = len(runs) * BATCH_ITERS / (ms / 1e3)
+    err = None
+    for i, p, d, m, g, lam in runs:
+        if i == fe["cube"]:
+            mg = m.cpu().numpy().astype(np.float64).reshape(mo.shape)
+            err = float(np.linalg.norm(mg - mo) / np.linalg.norm(mo))
+    out = {"value": round(rate, 3), "unit": "pairs/s",
+           "sample": f"{len(runs)} cubes spread over the fold range "
+                     f"({int(folds[picks[0]])}-{int(folds[picks[-1]])} traces), one single-cube "
+                     f"FP32 plan each, {BATCH_ITERS}-iteration FISTA per cube, one cube at a time",
+           "ms_per_pass": round(ms, 3),
+           "batched_over_per_cube": round(batched_value / rate, 3),
+           "fista_rel_l2_vs_fp64": err,
+           "fista_cube": fe["cube"]}
+    for _, p, d, m, _, _ in runs:
+        p.close()
+    return out
 
 
 # ------------------------------------------------------------- reference

@@ -153,6 +153,13 @@ typedef struct {
                            DFT along q; AAHRT_SLICE_DIRECT, or the tensor-core
                            contraction).  Not available with
                            AAHRT_SLICE_LINEAR_K or the pull scan. */
+    double r2max;       /* largest squared offset (m^2) the stretched-time
+                           plan is sized for (Sec. 3.4's no-wrap padding,
+                           through rho = |q|max r2max / tmax^2); 0 = the
+                           geometry's own.  A cube planned alone with the
+                           r2max of a batch gets the batch's time plan (Nfft,
+                           Ns, ds) and so the same operator.  Values below the
+                           geometry's own are refused (AAHRT_ERR_INVALID_ARG). */
 } aahrt_opts;
 
 /* What a plan chose (filled by aahrt_plan_query). */

@@ -42,7 +42,7 @@ class aahrt_opts(ctypes.Structure):
                 ("ngather", c_int), ("sigma_t", c_double), ("fmax", c_double),
                 ("time_pairs", c_int), ("autotune", c_int), ("precision", c_int),
                 ("slice_interp", c_int), ("sigma_q", c_double),
-                ("q_axis", POINTER(c_double))]
+                ("q_axis", POINTER(c_double)), ("r2max", c_double)]
 
 
 class aahrt_plan_info(ctypes.Structure):

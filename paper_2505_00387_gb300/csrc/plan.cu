@@ -327,6 +327,15 @@ int build_plan(Plan **out, int ncube, int ndist, const aahrt_geom *geoms,
     for (int c = 0; c < ndist; ++c)
         for (int h = 0; h < geoms[c].ntr; ++h)
             r2max = std::max(r2max, geoms[c].hx[h] * geoms[c].hx[h] + geoms[c].hy[h] * geoms[c].hy[h]);
+    if (opts.r2max != 0.0) {
+        if (!(opts.r2max >= r2max) || !std::isfinite(opts.r2max)) {
+            free_plan(p);
+            return set_error(AAHRT_ERR_INVALID_ARG,
+                             "opts.r2max %g is below the geometry's largest squared offset %g",
+                             opts.r2max, r2max);
+        }
+        r2max = opts.r2max;
+    }
     if (!(r2max > 0.0)) {
         free_plan(p);
         return set_error(AAHRT_ERR_INVALID_ARG, "all offsets are zero");

@@ -78,6 +78,29 @@ __device__ __forceinline__ void split8(const float *v, uint4 *hi, uint4 *lo) {
     split2(v[6], v[7], &hi->w, &lo->w);
 }
 
+// The two B-operand rows of complex values: the real-part row holds
+// (Re, -Im) and the imaginary-part row (Im, Re).  One hi/lo split of
+// (Re, Im) gives both: negate the high half, or swap the halves (bf16
+// negation is exact, so this equals splitting the negated value).
+__device__ __forceinline__ void split_cplx(float re, float im, uint32_t *rhi, uint32_t *rlo,
+                                           uint32_t *ihi, uint32_t *ilo) {
+    uint32_t h, l;
+    split2(re, im, &h, &l);
+    *rhi = h ^ 0x80000000u;
+    *rlo = l ^ 0x80000000u;
+    *ihi = __byte_perm(h, 0, 0x1032);
+    *ilo = __byte_perm(l, 0, 0x1032);
+}
+
+// a / d for 0 <= a < 2^20, d < 2^10, by a float reciprocal and one correction
+__device__ __forceinline__ int tc_div(int a, int d, float inv_d) {
+    int q = __float2int_rz(((float)a + 0.5f) * inv_d);
+    const int r = a - q * d;
+    if (r < 0) --q;
+    else if (r >= d) ++q;
+    return q;
+}
+
 // 16-byte chunk c (K-elements 8c .. 8c+7) of row r of a swizzled tile
 __device__ __forceinline__ void st_chunk(unsigned char *tile, int r, int c, uint4 v) {
     *reinterpret_cast<uint4 *>(tile + r * 128 + ((((unsigned)c ^ (unsigned)r) & 7u) << 4)) = v;
@@ -261,6 +284,7 @@ slice_fwd_tc_kernel(const TcArgs a, const float2 *__restrict__ X, float2 *__rest
     } else if (warp < kTcEpiWarp0) {
         // ---------------------------------------------------- producers
         const int pid = tid - 32 * kTcProdWarp0;
+        const float inv_gp = 1.0f / (float)Gp;
         uint32_t cc = 0;
         for (long long item = blockIdx.x; item < a.total && !*abort; item += gridDim.x) {
             const int k = (int)(item / a.ntiles);
@@ -303,36 +327,28 @@ slice_fwd_tc_kernel(const TcArgs a, const float2 *__restrict__ X, float2 *__rest
                     } else {
                         // B: rows (part, slice, g), K = the chunk's q samples
                         const int v = u - 128 * 4;
-                        const int g = v % Gp;
-                        const int rest = v / Gp;
+                        const int rest = tc_div(v, Gp, inv_gp);
+                        const int g = v - rest * Gp;
                         const int sl = rest & 1, lb = rest >> 1;
                         const float2 *Xs = sl ? Xn : Xj;
                         const int l0 = 32 * c + 8 * lb;
-                        float vr[16], vi[16];
+                        uint32_t rh[8], rl[8], ih[8], il[8];
 #pragma unroll
                         for (int i = 0; i < 8; ++i) {
                             const int l = l0 + i;
                             float2 x = make_float2(0.f, 0.f);
                             if (l < a.nq && g < a.G) x = __ldg(Xs + (long long)l * a.G + g);
-                            vr[2 * i] = x.x;
-                            vr[2 * i + 1] = -x.y;
-                            vi[2 * i] = x.y;
-                            vi[2 * i + 1] = x.x;
+                            split_cplx(x.x, x.y, &rh[i], &rl[i], &ih[i], &il[i]);
                         }
                         const int nre = sl * Gp + g, nim = 2 * Gp + sl * Gp + g;
-                        uint4 h0, lo0, h1, lo1;
-                        split8(vr, &h0, &lo0);
-                        split8(vr + 8, &h1, &lo1);
-                        st_chunk(bhi, nre, 2 * lb, h0);
-                        st_chunk(bhi, nre, 2 * lb + 1, h1);
-                        st_chunk(blo, nre, 2 * lb, lo0);
-                        st_chunk(blo, nre, 2 * lb + 1, lo1);
-                        split8(vi, &h0, &lo0);
-                        split8(vi + 8, &h1, &lo1);
-                        st_chunk(bhi, nim, 2 * lb, h0);
-                        st_chunk(bhi, nim, 2 * lb + 1, h1);
-                        st_chunk(blo, nim, 2 * lb, lo0);
-                        st_chunk(blo, nim, 2 * lb + 1, lo1);
+                        st_chunk(bhi, nre, 2 * lb, make_uint4(rh[0], rh[1], rh[2], rh[3]));
+                        st_chunk(bhi, nre, 2 * lb + 1, make_uint4(rh[4], rh[5], rh[6], rh[7]));
+                        st_chunk(blo, nre, 2 * lb, make_uint4(rl[0], rl[1], rl[2], rl[3]));
+                        st_chunk(blo, nre, 2 * lb + 1, make_uint4(rl[4], rl[5], rl[6], rl[7]));
+                        st_chunk(bhi, nim, 2 * lb, make_uint4(ih[0], ih[1], ih[2], ih[3]));
+                        st_chunk(bhi, nim, 2 * lb + 1, make_uint4(ih[4], ih[5], ih[6], ih[7]));
+                        st_chunk(blo, nim, 2 * lb, make_uint4(il[0], il[1], il[2], il[3]));
+                        st_chunk(blo, nim, 2 * lb + 1, make_uint4(il[4], il[5], il[6], il[7]));
                     }
                 }
                 fence_async_smem();     // this thread's tile writes -> the tensor core
@@ -466,6 +482,8 @@ slice_adj_tc_kernel(const TcArgs a, const float2 *__restrict__ Yh, float2 *__res
     } else if (warp < kTcEpiWarp0) {
         // ---------------------------------------------------- producers
         const int pid = tid - 32 * kTcProdWarp0;
+        const float inv_gp = 1.0f / (float)Gp;
+        const int na = 8 * 16 * nmt;     // A units: (4 traces, 8-q group)
         uint32_t cc = 0;
         for (long long item = blockIdx.x; item < a.total && !*abort; item += gridDim.x) {
             const int k = (int)(item / J);
@@ -477,7 +495,6 @@ slice_adj_tc_kernel(const TcArgs a, const float2 *__restrict__ Yh, float2 *__res
             const int nch = (ntot + 31) >> 5;
             const float2 *Ya = Yh + ((long long)a.nbins * a0 + (long long)k * n1) * a.G;
             const float2 *Yb = Yh + ((long long)a.nbins * b0 + (long long)k * n2) * a.G;
-            const int na = 32 * 16 * nmt;    // A units: (trace, 8-q group)
             for (int c = 0; c < nch; ++c, ++cc) {
                 const int st = cc & 1;
                 if (!tc_wait_bar(a, &bars.empty[st], ((cc >> 1) & 1) ^ 1, abort)) break;
@@ -485,39 +502,45 @@ slice_adj_tc_kernel(const TcArgs a, const float2 *__restrict__ Yh, float2 *__res
                 unsigned char *bhi = st0 + 4 * kTileA, *blo = bhi + bbytes;
                 for (int u = pid; u < na + 8 * Gp; u += kTcProdThreads) {
                     if (u < na) {
-                        // A: w conj(E)[l][h], rows l (M tiles), K = 32 traces
-                        const int hh = u & 31, lb = u >> 5;
-                        const int p = 32 * c + hh;
+                        // A: w conj(E)[l][h], rows l (M tiles), K = 32 traces: a
+                        // unit is 4 traces (one 16-byte chunk of a row) x 8 rows
+                        const int tq = u & 7, lb = u >> 3;
                         const int l0 = 8 * lb;
                         const int mt = l0 >> 7;
                         unsigned char *ahi = st0 + (2 * mt) * kTileA, *alo = ahi + kTileA;
-                        float2 e[8];
-                        if (p < ntot) {
-                            const TraceGeo tr = a.geo[p < n1 ? a0 + p : b0 + (p - n1)];
-                            const float wgt = p < n1 ? tr.w0 : tr.w1;
-                            if (a.qn)
-                                phases8_axis(tr, (unsigned)k, l0, a.qn, a.nq, 1.f, wgt, e);
-                            else
-                                phases8(tr, (unsigned)k, l0, a.cq, a.nq, 1.f, wgt, e);
-                        } else {
+                        float2 e[4][8];
 #pragma unroll
-                            for (int i = 0; i < 8; ++i) e[i] = make_float2(0.f, 0.f);
+                        for (int tt = 0; tt < 4; ++tt) {
+                            const int p = 32 * c + 4 * tq + tt;
+                            if (p < ntot) {
+                                const TraceGeo tr = a.geo[p < n1 ? a0 + p : b0 + (p - n1)];
+                                const float wgt = p < n1 ? tr.w0 : tr.w1;
+                                if (a.qn)
+                                    phases8_axis(tr, (unsigned)k, l0, a.qn, a.nq, 1.f, wgt, e[tt]);
+                                else
+                                    phases8(tr, (unsigned)k, l0, a.cq, a.nq, 1.f, wgt, e[tt]);
+                            } else {
+#pragma unroll
+                                for (int i = 0; i < 8; ++i) e[tt][i] = make_float2(0.f, 0.f);
+                            }
                         }
 #pragma unroll
                         for (int i = 0; i < 8; ++i) {
-                            const int r = (l0 & 127) + i;
-                            uint32_t h, lo;
-                            split2(e[i].x, e[i].y, &h, &lo);
-                            const uint32_t off = sw128_offset((uint32_t)r, (uint32_t)(2 * hh));
-                            *reinterpret_cast<uint32_t *>(ahi + off) = h;
-                            *reinterpret_cast<uint32_t *>(alo + off) = lo;
+                            uint4 h, lo;
+                            split2(e[0][i].x, e[0][i].y, &h.x, &lo.x);
+                            split2(e[1][i].x, e[1][i].y, &h.y, &lo.y);
+                            split2(e[2][i].x, e[2][i].y, &h.z, &lo.z);
+                            split2(e[3][i].x, e[3][i].y, &h.w, &lo.w);
+                            st_chunk(ahi, (l0 & 127) + i, tq, h);
+                            st_chunk(alo, (l0 & 127) + i, tq, lo);
                         }
                     } else {
                         // B: rows (part, g), K = 32 traces x (Re, Im); one unit is
                         // one 16-byte chunk (4 traces) of a row pair
                         const int v = u - na;
-                        const int g = v % Gp, tq = v / Gp;
-                        float vr[8], vi[8];
+                        const int tq = tc_div(v, Gp, inv_gp);
+                        const int g = v - tq * Gp;
+                        uint32_t rh[4], rl[4], ih[4], il[4];
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
                             const int p = 32 * c + 4 * tq + i;
@@ -525,18 +548,12 @@ slice_adj_tc_kernel(const TcArgs a, const float2 *__restrict__ Yh, float2 *__res
                             if (p < ntot && g < a.G)
                                 y = __ldg(p < n1 ? Ya + (long long)p * a.G + g
                                                  : Yb + (long long)(p - n1) * a.G + g);
-                            vr[2 * i] = y.x;
-                            vr[2 * i + 1] = -y.y;
-                            vi[2 * i] = y.y;
-                            vi[2 * i + 1] = y.x;
+                            split_cplx(y.x, y.y, &rh[i], &rl[i], &ih[i], &il[i]);
                         }
-                        uint4 h, lo;
-                        split8(vr, &h, &lo);
-                        st_chunk(bhi, g, tq, h);
-                        st_chunk(blo, g, tq, lo);
-                        split8(vi, &h, &lo);
-                        st_chunk(bhi, Gp + g, tq, h);
-                        st_chunk(blo, Gp + g, tq, lo);
+                        st_chunk(bhi, g, tq, make_uint4(rh[0], rh[1], rh[2], rh[3]));
+                        st_chunk(blo, g, tq, make_uint4(rl[0], rl[1], rl[2], rl[3]));
+                        st_chunk(bhi, Gp + g, tq, make_uint4(ih[0], ih[1], ih[2], ih[3]));
+                        st_chunk(blo, Gp + g, tq, make_uint4(il[0], il[1], il[2], il[3]));
                     }
                 }
                 fence_async_smem();

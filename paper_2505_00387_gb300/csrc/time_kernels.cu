@@ -172,6 +172,9 @@ __device__ __forceinline__ void r2c_core(float2 *sm, const float *stg, const flo
         for (int c = threadIdx.x; c < ybd.nchunk; c += blockDim.x) s_ymax[c] = 0u;
         __syncthreads();
     }
+    // rows 16-byte aligned (even row stride and offset): a column pair's A and
+    // B leave as one 16-byte store
+    const bool wide = ((cg.ld_spec | cg.spec_off) & 1) == 0;
     const int kend = ((P * nbins + blockDim.x - 1) / blockDim.x) * blockDim.x;
     for (int idx = threadIdx.x; idx < kend; idx += blockDim.x) {
         const int p = idx & (P - 1);
@@ -183,11 +186,17 @@ __device__ __forceinline__ void r2c_core(float2 *sm, const float *stg, const flo
             const float2 A = make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
             const float2 B = make_float2(0.5f * (zk.y + zn.y), -0.5f * (zk.x - zn.x));
             const long long o = (long long)k * cg.ld_spec + 2 * p;
-            dst[o] = A;
             amax = fabsf(A.x) + fabsf(A.y);
             if (2 * p + 1 < cg.ncol) {
-                dst[o + 1] = B;
+                if (wide)
+                    *reinterpret_cast<float4 *>(dst + o) = make_float4(A.x, A.y, B.x, B.y);
+                else {
+                    dst[o] = A;
+                    dst[o + 1] = B;
+                }
                 amax = fmaxf(amax, fabsf(B.x) + fabsf(B.y));
+            } else {
+                dst[o] = A;
             }
         }
         if (bound) {
@@ -274,6 +283,8 @@ __device__ __forceinline__ void c2r_core(float2 *sm, float *sfr, const float2 *_
     // kPackBatch rounds of loads are issued before any is used, so each
     // thread keeps that many spectrum reads in flight
     const int total = P * (half + 1);
+    // rows 16-byte aligned: a column pair's A and B arrive as one 16-byte load
+    const bool wide = ((cg.ld_spec | cg.spec_off) & 1) == 0;
     for (int base = threadIdx.x; base < total; base += kPackBatch * blockDim.x) {
         float2 A[kPackBatch], B[kPackBatch];
 #pragma unroll
@@ -285,8 +296,15 @@ __device__ __forceinline__ void c2r_core(float2 *sm, float *sfr, const float2 *_
             if (idx < total && k < nbins && p < npair) {
                 const long long o = (long long)k * cg.ld_spec + 2 * p;
                 // the fused kernel rewrites the spectrum later: plain loads there
-                A[u] = STAGE ? src[o] : __ldg(src + o);
-                if (2 * p + 1 < cg.ncol) B[u] = STAGE ? src[o + 1] : __ldg(src + o + 1);
+                if (wide && 2 * p + 1 < cg.ncol) {
+                    const float4 *q4 = reinterpret_cast<const float4 *>(src + o);
+                    const float4 v = STAGE ? *q4 : __ldg(q4);
+                    A[u] = make_float2(v.x, v.y);
+                    B[u] = make_float2(v.z, v.w);
+                } else {
+                    A[u] = STAGE ? src[o] : __ldg(src + o);
+                    if (2 * p + 1 < cg.ncol) B[u] = STAGE ? src[o + 1] : __ldg(src + o + 1);
+                }
             }
         }
 #pragma unroll

@@ -39,7 +39,7 @@ SLICE_INTERPS = {"spread": L.AAHRT_SLICE_SPREAD, "linear_k": L.AAHRT_SLICE_LINEA
 
 def _opts(interp="keys", spread_width=0, theta_group=0, ngather=1, sigma_t=0.0, fmax=0.0,
           time_pairs=0, autotune=False, precision="fp32", slice_interp="spread",
-          sigma_q=0.0, q_axis=None, keep=None):
+          sigma_q=0.0, q_axis=None, keep=None, r2max=0.0):
     kind = {"keys": L.AAHRT_INTERP_KEYS, "linear": L.AAHRT_INTERP_LINEAR}[interp]
     qp = None
     if q_axis is not None:
@@ -52,7 +52,7 @@ def _opts(interp="keys", spread_width=0, theta_group=0, ngather=1, sigma_t=0.0, 
     return L.aahrt_opts(kind, int(spread_width), int(theta_group), int(ngather),
                         float(sigma_t), float(fmax), int(time_pairs), int(bool(autotune)),
                         PRECISIONS[precision], SLICE_INTERPS[slice_interp], float(sigma_q),
-                        qp)
+                        qp, float(r2max))
 
 
 def q_axis_slowness(pmin: float, pmax: float, nq: int) -> np.ndarray:
@@ -71,7 +71,7 @@ class AahrtPlan:
     def __init__(self, nt, dt, ntau, nq, q0, dq, ntheta, hx, hy, *, interp="keys",
                  spread_width=0, theta_group=0, ngather=1, sigma_t=0.0, fmax=0.0,
                  time_pairs=0, autotune=False, precision="fp32", slice_interp="spread",
-                 sigma_q=0.0, q_axis=None, _handle=None, _shapes=None):
+                 sigma_q=0.0, q_axis=None, r2max=0.0, _handle=None, _shapes=None):
         if _handle is not None:
             self.handle = _handle
         else:
@@ -80,7 +80,7 @@ class AahrtPlan:
             self.handle = L.aahrt_plan_create(
                 g, _opts(interp, spread_width, theta_group, ngather, sigma_t, fmax,
                          time_pairs, autotune, precision, slice_interp, sigma_q, q_axis,
-                         keep))
+                         keep, r2max))
         self.info = L.aahrt_plan_query(self.handle)
         self.nt, self.ntau, self.nq, self.ntheta = nt, ntau, nq, ntheta
         self.device = torch.device("cuda", torch.cuda.current_device())
@@ -92,13 +92,13 @@ class AahrtPlan:
     @classmethod
     def batched(cls, gathers: Sequence, interp="keys", spread_width=0, theta_group=0,
                 sigma_t=0.0, fmax=0.0, time_pairs=0, autotune=False, slice_interp="spread",
-                sigma_q=0.0, q_axis=None):
+                sigma_q=0.0, q_axis=None, r2max=0.0):
         keep = []
         geoms = [_geom(g.nt, g.dt, g.ntau, g.nq, g.q0, g.dq, g.ntheta, g.hx, g.hy, keep)
                  for g in gathers]
         h = L.aahrt_plan_create_batched(
             geoms, _opts(interp, spread_width, theta_group, 1, sigma_t, fmax, time_pairs,
-                         autotune, "fp32", slice_interp, sigma_q, q_axis, keep))
+                         autotune, "fp32", slice_interp, sigma_q, q_axis, keep, r2max))
         g0 = gathers[0]
         return cls(g0.nt, g0.dt, g0.ntau, g0.nq, g0.q0, g0.dq, g0.ntheta, None, None,
                    _handle=h)

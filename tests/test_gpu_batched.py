@@ -170,3 +170,37 @@ def test_batch512_sampled_parity():
         c, p = cs[i], ops_[i]
         ref = fista.solve(p, c.d, est_l[i], 50, est_g[i])
         assert rel(ms[i].reshape(ref.shape), ref) <= TOL_SOLVE
+
+
+def test_single_cube_on_the_batch_time_plan():
+    """A cube planned alone with the batch's largest squared offset (opts
+    r2max) gets the batch's stretched-time plan and so the same operator:
+    its forward and adjoint equal the batched plan's on that cube (the
+    per-cube form of the same work).  An r2max below the
+    cube's own offsets is refused."""
+    from paper_2505_00387_gb300 import _lib as L
+    from paper_2505_00387_gb300.plan import AahrtPlan
+    cs, _ = small_batch()
+    r2max = max(float(np.max(c.hx ** 2 + c.hy ** 2)) for c in cs)
+    bp = AahrtPlan.batched(cs)
+    i = int(np.argmin([float(np.max(x.hx ** 2 + x.hy ** 2)) for x in cs]))
+    c = cs[i]
+    assert float(np.max(c.hx ** 2 + c.hy ** 2)) < r2max
+    sp = AahrtPlan(**c.geom_kwargs(), r2max=r2max)
+    for f in ("nfft", "ns", "nbins", "spread_width"):
+        assert getattr(sp.info, f) == getattr(bp.info, f), f
+    assert sp.info.ds == bp.info.ds
+    own = AahrtPlan(**c.geom_kwargs())
+    assert own.info.rho < sp.info.rho
+    rng = np.random.default_rng(71)
+    ms = [rng.standard_normal((x.ntau, x.nq, x.ntheta)) for x in cs]
+    ds = [rng.standard_normal((x.nt, x.ntr)) for x in cs]
+    dg = split(host(bp.forward(dev(np.concatenate([m.ravel() for m in ms])))),
+               [x.nt * x.ntr for x in cs])
+    mg = split(host(bp.adjoint(dev(np.concatenate([d.ravel() for d in ds])))),
+               [m.size for m in ms])
+    assert rel(host(sp.forward(dev(ms[i]))), dg[i]) < 1e-6
+    assert rel(host(sp.adjoint(dev(ds[i]))), mg[i]) < 1e-6
+    with pytest.raises(L.AahrtError) as e:
+        AahrtPlan(**c.geom_kwargs(), r2max=0.5 * float(np.max(c.hx ** 2 + c.hy ** 2)))
+    assert e.value.status == L.AAHRT_ERR_INVALID_ARG
