@@ -483,7 +483,7 @@ slice_adj_tc_kernel(const TcArgs a, const float2 *__restrict__ Yh, float2 *__res
         // ---------------------------------------------------- producers
         const int pid = tid - 32 * kTcProdWarp0;
         const float inv_gp = 1.0f / (float)Gp;
-        const int na = 8 * 16 * nmt;     // A units: (4 traces, 8-q group)
+        const int na = 32 * 16 * nmt;    // A units: (trace, 8-q group)
         uint32_t cc = 0;
         for (long long item = blockIdx.x; item < a.total && !*abort; item += gridDim.x) {
             const int k = (int)(item / J);
@@ -502,37 +502,32 @@ slice_adj_tc_kernel(const TcArgs a, const float2 *__restrict__ Yh, float2 *__res
                 unsigned char *bhi = st0 + 4 * kTileA, *blo = bhi + bbytes;
                 for (int u = pid; u < na + 8 * Gp; u += kTcProdThreads) {
                     if (u < na) {
-                        // A: w conj(E)[l][h], rows l (M tiles), K = 32 traces: a
-                        // unit is 4 traces (one 16-byte chunk of a row) x 8 rows
-                        const int tq = u & 7, lb = u >> 3;
+                        // A: w conj(E)[l][h], rows l (M tiles), K = 32 traces
+                        const int hh = u & 31, lb = u >> 5;
+                        const int p = 32 * c + hh;
                         const int l0 = 8 * lb;
                         const int mt = l0 >> 7;
                         unsigned char *ahi = st0 + (2 * mt) * kTileA, *alo = ahi + kTileA;
-                        float2 e[4][8];
+                        float2 e[8];
+                        if (p < ntot) {
+                            const TraceGeo tr = a.geo[p < n1 ? a0 + p : b0 + (p - n1)];
+                            const float wgt = p < n1 ? tr.w0 : tr.w1;
+                            if (a.qn)
+                                phases8_axis(tr, (unsigned)k, l0, a.qn, a.nq, 1.f, wgt, e);
+                            else
+                                phases8(tr, (unsigned)k, l0, a.cq, a.nq, 1.f, wgt, e);
+                        } else {
 #pragma unroll
-                        for (int tt = 0; tt < 4; ++tt) {
-                            const int p = 32 * c + 4 * tq + tt;
-                            if (p < ntot) {
-                                const TraceGeo tr = a.geo[p < n1 ? a0 + p : b0 + (p - n1)];
-                                const float wgt = p < n1 ? tr.w0 : tr.w1;
-                                if (a.qn)
-                                    phases8_axis(tr, (unsigned)k, l0, a.qn, a.nq, 1.f, wgt, e[tt]);
-                                else
-                                    phases8(tr, (unsigned)k, l0, a.cq, a.nq, 1.f, wgt, e[tt]);
-                            } else {
-#pragma unroll
-                                for (int i = 0; i < 8; ++i) e[tt][i] = make_float2(0.f, 0.f);
-                            }
+                            for (int i = 0; i < 8; ++i) e[i] = make_float2(0.f, 0.f);
                         }
 #pragma unroll
                         for (int i = 0; i < 8; ++i) {
-                            uint4 h, lo;
-                            split2(e[0][i].x, e[0][i].y, &h.x, &lo.x);
-                            split2(e[1][i].x, e[1][i].y, &h.y, &lo.y);
-                            split2(e[2][i].x, e[2][i].y, &h.z, &lo.z);
-                            split2(e[3][i].x, e[3][i].y, &h.w, &lo.w);
-                            st_chunk(ahi, (l0 & 127) + i, tq, h);
-                            st_chunk(alo, (l0 & 127) + i, tq, lo);
+                            const int r = (l0 & 127) + i;
+                            uint32_t h, lo;
+                            split2(e[i].x, e[i].y, &h, &lo);
+                            const uint32_t off = sw128_offset((uint32_t)r, (uint32_t)(2 * hh));
+                            *reinterpret_cast<uint32_t *>(ahi + off) = h;
+                            *reinterpret_cast<uint32_t *>(alo + off) = lo;
                         }
                     } else {
                         // B: rows (part, g), K = 32 traces x (Re, Im); one unit is
