@@ -465,14 +465,16 @@ def measure(kind, args, rank, world, dev):
         "clocks": clocks,
     }
     if not slow:
-        # the slice steps' own bound: issue slots and the FP32 pipe (ncu, one
-        # launch of each kernel on the same workload shape, while the sources
-        # still hash to the captured ones)
+        # the slice steps' own bound: the L1 / shared-memory data pipe, with
+        # the issue slots and the FP32 pipe beside it (ncu, one launch of each
+        # kernel on the same workload shape, while the sources still hash to
+        # the captured ones)
         alu = {}
         for st in ("slice_fwd", "slice_adj"):
             r = traffic_record(st + suffix)
             if r and "issue_active" in r:
-                alu[st] = {"issue_active": r["issue_active"], "fma_pipe": r.get("fma_pipe"),
+                alu[st] = {"l1_data_pipe": r.get("l1_data_pipe"),
+                           "issue_active": r["issue_active"], "fma_pipe": r.get("fma_pipe"),
                            "kernel": r["kernel"]}
         if alu:
             line["slice_issue"] = alu
