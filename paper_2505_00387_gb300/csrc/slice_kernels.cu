@@ -111,8 +111,12 @@ slice_fwd_kernel(const SliceArgs a, const float2 *__restrict__ X, float2 *__rest
         // interpolate every owned trace
         const TraceGeo *geo = a.geo + g.geo_off;
         float2 *Yk = Y + g.y_off + (long long)k * g.ntr;
+        // the next trace's record is loaded while this one is interpolated
+        TraceGeo nxt{};
+        if (g.f0 + (int)threadIdx.x < g.f1) nxt = geo[g.f0 + threadIdx.x];
         for (int t = g.f0 + threadIdx.x; t < g.f1; t += blockDim.x) {
-            const TraceGeo tr = geo[t];
+            const TraceGeo tr = nxt;
+            if (t + (int)blockDim.x < g.f1) nxt = geo[t + blockDim.x];
             const TapSet ts = trace_taps<W>(tr.A, tr.B, (unsigned)k, a.Lq);
             float phi[W];
             es_weights<W>(a.poly, ts.g, phi);
@@ -149,13 +153,12 @@ slice_fwd_kernel(const SliceArgs a, const float2 *__restrict__ X, float2 *__rest
 
 template <int W>
 __device__ __forceinline__ void spread_trace(const SliceArgs &a, const SliceGroup &g,
-                                             const TraceGeo &tr, const float2 *Yk, int k,
+                                             const TraceGeo &tr, float2 y, int k,
                                              int *Gre, int *Gim, int lds, int mask,
                                              const float *fx) {
     const TapSet ts = trace_taps<W>(tr.A, tr.B, (unsigned)k, a.Lq);
     float phi[W];
     es_weights<W>(a.poly, ts.g, phi);
-    const float2 y = __ldg(Yk + tr.col);
     float sn, cs;
     phase_cs(ts.ph, &sn, &cs);
     // scale * y * exp(+2 pi i ph)
@@ -298,10 +301,19 @@ slice_adj_kernel(const SliceArgs a, const float2 *__restrict__ Y, float2 *__rest
         }
         __syncthreads();
 
-        for (int t = g.f0 + threadIdx.x; t < g.f1; t += blockDim.x)
-            spread_trace<W>(a, g, geo[t], Yk, k, Ire, Iim, lds, mask, s_fx);
-        for (int t = g.e0 + threadIdx.x; t < g.e1; t += blockDim.x)
-            spread_trace<W>(a, g, geo[t], Yk, k, Ire, Iim, lds, mask, s_fx);
+        // the next trace's record is loaded while this one is spread, and
+        // this one's y at the top, ahead of the taps and weights
+        for (int r = 0; r < 2; ++r) {
+            const int t0 = r == 0 ? g.f0 : g.e0, t1 = r == 0 ? g.f1 : g.e1;
+            TraceGeo nxt{};
+            if (t0 + (int)threadIdx.x < t1) nxt = geo[t0 + threadIdx.x];
+            for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+                const TraceGeo tr = nxt;
+                const float2 y = __ldg(Yk + tr.col);
+                if (t + (int)blockDim.x < t1) nxt = geo[t + blockDim.x];
+                spread_trace<W>(a, g, tr, y, k, Ire, Iim, lds, mask, s_fx);
+            }
+        }
         __syncthreads();
         if (a.Lq >= 5) {
             adj_first_step(a, g, smf, lds, s_ifx);
