@@ -202,9 +202,14 @@ __device__ __forceinline__ void adj_first_step(const SliceArgs &a, const SliceGr
     float *Gre = smf, *Gim = smf + g.nj * lds;
     const int *Ire = reinterpret_cast<const int *>(Gre);
     const int *Iim = reinterpret_cast<const int *>(Gim);
+    // the column (slice) varies fastest across a warp's lanes: with the
+    // column stride lds = 1 modulo the bank count, consecutive columns fall
+    // in consecutive banks (at most 2-way conflicts, against 4-way when a warp
+    // covered 4 columns x 8 groups)
+    const float inv_nj = 1.0f / (float)g.nj;
     for (int w = threadIdx.x; w < ng * g.nj; w += blockDim.x) {
-        const int jj = w >> lhs;
-        const int j = w & (ng - 1);
+        const int j = fast_div(w, g.nj, inv_nj);
+        const int jj = w - j * g.nj;
         const float f = ifx[jj];
         const int pb = jj * lds + padi(j);
         float2 v[16];
