@@ -190,6 +190,29 @@ def test_edge_cases(case):
     assert _dot_test(gp, p, 41) < TOL_DOT
 
 
+# q grids of nos = 32, 128 and 512 points (the adjoint's inverse q-FFT as a
+# first and a last step, or with middle steps); one azimuth group with the
+# wrap from the last slice to slice 0, or groups of 2 slices with edge traces;
+# up to 2600 traces (ten per thread) in one work item
+@pytest.mark.parametrize("nq,ntr,nth,tg", [(9, 700, 4, 0), (37, 2600, 3, 0), (37, 2600, 6, 2),
+                                           (150, 400, 4, 2)])
+def test_adjoint_grid_sizes_and_repeatability(nq, ntr, nth, tg):
+    """Adjoint parity across q-grid sizes and group layouts, and bitwise
+    repeatable output: the spread's shared-memory integer atomics land in
+    whatever order the warps reach them, and the sums must not depend on it."""
+    g = _ragged_gather(ntr=ntr, nq=nq, nth=nth, seed=33)
+    p = oracle_plan(g)
+    gp = gpu_plan(g, theta_group=tg)
+    rng = np.random.default_rng(34)
+    d = rng.standard_normal((g.nt, g.ntr))
+    shape = (g.ntau, g.nq, g.ntheta)
+    m1 = host(gp.adjoint(dev(d)), shape)
+    m2 = host(gp.adjoint(dev(d)), shape)
+    np.testing.assert_array_equal(m1, m2)
+    assert rel(m1, ops.adjoint(p, d)) < TOL_OP
+    assert _dot_test(gp, p, 35) < TOL_DOT
+
+
 def test_plan_refuses_oversized_frame():
     from paper_2505_00387_gb300 import _lib as L
     g = _ragged_gather(nt=8, ntr=5, nq=3, nth=2)
