@@ -52,10 +52,6 @@ __host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) {
 __host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
-// a * conj(b)
-__host__ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
-    return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
-}
 
 __host__ __device__ __forceinline__ unsigned brev_bits(unsigned x, int L) {
 #ifdef __CUDA_ARCH__

@@ -27,15 +27,14 @@
 
 namespace aahrt {
 
-__device__ __forceinline__ RowPos load_pos(const RowPos *p) {
-    const int2 v = __ldg(reinterpret_cast<const int2 *>(p));
-    return RowPos{v.x, __int_as_float(v.y)};
-}
-// Transposed row: sources lo, lo+1, ... in segments of decreasing tap t
-// (largest t first); segment q (tap t0 + q) has (cnt >> 8q) & 255 rows.
-__device__ __forceinline__ RowRange load_rng(const RowRange *p) {
-    const int2 v = __ldg(reinterpret_cast<const int2 *>(p));
-    return RowRange{v.x, v.y};
+// Entry i of a resampler's row table, as its two raw words: a RowPos
+// (fl, bits of fr) for S or U, a RowRange for S^T or U^T (sources lo, lo+1,
+// ... in segments of decreasing tap t, largest t first; segment q, tap
+// t0 + q, has (cnt >> 8q) & 255 rows).
+template <bool TRANS>
+__device__ __forceinline__ int2 row_entry(const DevResampler &rs, int i) {
+    return __ldg(reinterpret_cast<const int2 *>(TRANS ? (const void *)(rs.rng + i)
+                                                      : (const void *)(rs.pos + i)));
 }
 
 constexpr int kPackBatch = 8;   // spectrum loads in flight per thread (c2r pack)
@@ -125,16 +124,13 @@ __device__ __forceinline__ void r2c_core(float2 *sm, const float *stg, const flo
     // the next row's table entry is loaded while this row is resampled
     int2 nxt = make_int2(0, 0);
     if ((int)threadIdx.x < rs.nrows)
-        nxt = __ldg(reinterpret_cast<const int2 *>(TRANS ? (const void *)(rs.rng + threadIdx.x)
-                                                         : (const void *)(rs.pos + threadIdx.x)));
+        nxt = row_entry<TRANS>(rs, threadIdx.x);
     for (int n = threadIdx.x; n < N; n += blockDim.x) {
         Acc<P> acc;
         acc.zero();
         const int2 cur = nxt;
         if (n + (int)blockDim.x < rs.nrows)
-            nxt = __ldg(reinterpret_cast<const int2 *>(
-                TRANS ? (const void *)(rs.rng + n + blockDim.x)
-                      : (const void *)(rs.pos + n + blockDim.x)));
+            nxt = row_entry<TRANS>(rs, n + blockDim.x);
         if (n < rs.nrows) {
             if (!TRANS) {
                 const RowPos ps{cur.x, __int_as_float(cur.y)};
@@ -340,16 +336,13 @@ __device__ __forceinline__ void c2r_core(float2 *sm, float *sfr, const float2 *_
     // thread; the next row's table entry is loaded while this one is done
     int2 nxt = make_int2(0, 0);
     if ((int)threadIdx.x < rs.nrows)
-        nxt = __ldg(reinterpret_cast<const int2 *>(TRANS ? (const void *)(rs.rng + threadIdx.x)
-                                                         : (const void *)(rs.pos + threadIdx.x)));
+        nxt = row_entry<TRANS>(rs, threadIdx.x);
     for (int i = threadIdx.x; i < rs.nrows; i += blockDim.x) {
         Acc<P> acc;
         acc.zero();
         const int2 cur = nxt;
         if (i + (int)blockDim.x < rs.nrows)
-            nxt = __ldg(reinterpret_cast<const int2 *>(
-                TRANS ? (const void *)(rs.rng + i + blockDim.x)
-                      : (const void *)(rs.pos + i + blockDim.x)));
+            nxt = row_entry<TRANS>(rs, i + blockDim.x);
         const long long o = cg.real_off + (long long)i * cg.ld_real;
         const int nc = cg.ncol;
         // the FISTA update's m row is loaded first, its latency covered by
