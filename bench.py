@@ -12,7 +12,9 @@ far beyond L2, and L2 is flushed between timed steps); `e2e` passes pinned
 host buffers to the C ABI so the host<->device copies of d and m are inside
 the timed region.  The same JSON line carries, under "gather", the line of
 the paper-scale single gather (nt = 1001, 2000 traces in a 3 km disc, 100
-curvatures x 36 azimuths; one step = one 100-iteration FISTA solve).
+curvatures x 36 azimuths; one step = one 100-iteration FISTA solve) and, on
+one GPU, under "slowness" and "shared64", the lines of the two workloads
+below (the shared-geometry one with at most 5 timed steps).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                   [--workload batch512|gather|slowness|table1|shared64]
@@ -55,6 +57,7 @@ BATCH_ITERS = 50
 BATCH_WORKLOAD = ("512 CMP cubes: nt=1001 dt=4ms, fold 200-3000 in 90-360 degree sectors "
                   "of a 3 km disc, 64 q x 24 azimuths, one autotuned plan; one step = one "
                   "50-iteration FISTA solve of every cube (per-cube step and threshold)")
+NESTED_STEPS = 5
 L2_NOTE = "inputs far larger than L2 (spectra of tens of GB), and L2 flushed (256 MB write)"
 L2_NOTE_GATHER = "L2 flushed between timed steps (256 MB write)"
 
@@ -276,6 +279,16 @@ def run_ours(args):
     if args.workload == "batch512":
         # the paper-scale single gather, measured the same way in the same run
         line["gather"] = measure("gather", args, rank, world, dev)
+        if world == 1:
+            # one GPU: the other two workloads of the bench in the same run, the
+            # gather on the uniform slowness axis and the 64 shared-geometry
+            # gathers (at most NESTED_STEPS timed steps each)
+            import torch
+            torch.cuda.empty_cache()
+            line["slowness"] = measure("slowness", args, rank, world, dev)
+            torch.cuda.empty_cache()
+            line["shared64"] = measure_shared64(args, rank, min(args.steps, NESTED_STEPS))
+            torch.cuda.empty_cache()
     if world > 1:
         dist.destroy_process_group()
     if rank == 0:
@@ -915,20 +928,50 @@ def tc_flops(hx, hy, nq, ntheta, nbins, G):
 
 
 def run_shared64(args):
-    """Forward + adjoint of 64 gathers sharing one geometry (8000 traces in a
-    4 km disc, nt = 2048 at 2 ms, 200 q x 72 azimuths), three ways: the
-    split-BF16 tensor-core contraction of all 64 in one plan, the FP32
-    spreading path of all 64 in one plan, and one single-gather FP32 plan
-    applied to the 64 gathers in turn (the plain per-gather form).  Errors of
-    each against the FP64 checker on sampled traces (forward) and azimuth
-    slices (adjoint) of two gathers."""
-    import numpy as np
+    """--workload shared64: the shared-geometry line alone."""
     import torch
 
     rank, world, local = dist_info()
     torch.cuda.set_device(local)
     from paper_2505_00387_gb300 import build as B
     B.build()
+    line = measure_shared64(args, rank, args.steps)
+    print(json.dumps(line), flush=True)
+
+
+def gpu_dot_rel(fwd, adj, m, seed):
+    """FP32 dot test of a GPU operator pair, inner products accumulated in
+    FP64: m given, d = L m plus as much independent noise (so <L m, d> is about
+    |L m|^2, not a near-zero random projection), and
+    |<L m, d> - <m, L^T d>| / |<L m, d>|."""
+    import torch
+
+    def dot64(a, b, chunk=1 << 26):
+        a, b = a.reshape(-1), b.reshape(-1)
+        return sum(float(torch.dot(a[i:i + chunk].double(), b[i:i + chunk].double()))
+                   for i in range(0, a.numel(), chunk))
+
+    lm = fwd(m)
+    gen = torch.Generator(device=m.device).manual_seed(seed)
+    d = torch.randn(lm.shape, device=m.device, generator=gen)
+    d.mul_((dot64(lm, lm) / lm.numel()) ** 0.5).add_(lm)
+    lhs = dot64(lm, d)
+    del lm
+    rhs = dot64(m, adj(d))
+    return abs(lhs - rhs) / abs(lhs)
+
+
+def measure_shared64(args, rank, steps):
+    """Forward + adjoint of 64 gathers sharing one geometry (8000 traces in a
+    4 km disc, nt = 2048 at 2 ms, 200 q x 72 azimuths), three ways: the
+    split-BF16 tensor-core contraction of all 64 in one plan, the FP32
+    spreading path of all 64 in one plan, and one single-gather FP32 plan
+    applied to the 64 gathers in turn (the plain per-gather form).  Errors of
+    each against the FP64 checker on sampled traces (forward) and azimuth
+    slices (adjoint) of two gathers, and each form's FP32 dot test."""
+    import numpy as np
+    import torch
+
     from paper_2505_00387_gb300 import _lib as L
     from paper_2505_00387_gb300 import synthetic as syn
     from paper_2505_00387_gb300.plan import AahrtPlan
@@ -964,14 +1007,14 @@ def run_shared64(args):
             pair()
         torch.cuda.synchronize()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.steps)]
+              for _ in range(steps)]
         for e0, e1 in ev:
             flush.zero_()
             e0.record()
             pair()
             e1.record()
         torch.cuda.synchronize()
-        return sum(a.elapsed_time(b) for a, b in ev) / args.steps
+        return sum(a.elapsed_time(b) for a, b in ev) / steps
 
     res = {}
     for prec in ("split_bf16", "fp32"):
@@ -988,7 +1031,7 @@ def run_shared64(args):
             gp.adjoint(d, mo)
         ms_pair = timed_steps(pair)
         gp.set_profiling(True)
-        for _ in range(args.steps):
+        for _ in range(steps):
             pair()
         torch.cuda.synchronize()
         t, n = gp.stage_times()
@@ -1026,7 +1069,10 @@ def run_shared64(args):
                      "gather_pairs_per_s": round(G / (ms_pair / 1e3), 2),
                      "stages_ms": {L.STAGE_NAMES[i]: round(t[i] / n[i], 3)
                                    for i in range(6) if n[i]},
-                     "nbins": gp.info.nbins}
+                     "nbins": gp.info.nbins,
+                     "dot_test_rel": gpu_dot_rel(gp.forward, gp.adjoint, m, 11)}
+        if tc:
+            gp.status()
         if err:
             res[prec]["err_vs_fp64"] = {
                 "forward_rel_l2_max": max(e[0] for e in err.values()),
@@ -1057,6 +1103,7 @@ def run_shared64(args):
                        rel(mg.reshape(shape_m)[:, :, slices].astype(np.float64), ref[i][1]))
     res["fp32_per_gather"] = {"ms_per_pair": round(ms1, 3),
                               "gather_pairs_per_s": round(G / (ms1 / 1e3), 2),
+                              "dot_test_rel": gpu_dot_rel(g1.forward, g1.adjoint, m1[0], 11),
                               "form": "one single-gather FP32 plan, forward + adjoint of the 64 "
                                       "gathers one after another"}
     if err1:
@@ -1076,10 +1123,14 @@ def run_shared64(args):
     t_f, t_a = tc["stages_ms"]["slice_fwd"], tc["stages_ms"]["slice_adj"]
     top, fl, tt = ("slice_adj", fa, t_a) if t_a >= t_f else ("slice_fwd", ff, t_f)
     ach = fl / (tt * 1e-3) / 1e12
+    # DRAM bytes per launch from the committed ncu record of the same kernel
+    # (a 256-bin case of this geometry scaled to these bins), while its
+    # sources still hash to the captured ones
+    trec = traffic_record(top + "@shared64")
     line = {"metric": "shared-geometry gathers: forward+adjoint pairs/s, split-BF16 tensor cores "
                       "vs FP32 spreading (batched and per gather)",
             "value": tc["gather_pairs_per_s"], "unit": "gather-pairs/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": max(args.warmup, 3),
+            "steps": steps, "warmup": max(args.warmup, 3),
             "ms_per_step": tc["ms_per_pair"], "higher_is_better": True, "vs_baseline": None,
             "dtype": "bf16x3 (split) / f32 accumulate", "data": "synthetic (seeded random m, d)",
             "config": {"workload": "64 gathers on one geometry: 8000 traces in a 4 km disc, "
@@ -1087,7 +1138,9 @@ def run_shared64(args):
                                    "adjoint of all gathers",
                        "l2": "spectra (tens of GB) far beyond L2, and flushed"},
             "roofline": {"bound": "tensor", "achieved": round(ach, 1), "peak": peak,
-                         "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
+                         "unit": "TFLOP/s", "frac": round(ach / peak, 4),
+                         "traffic": trec.get("dram_bytes") if trec else None,
+                         "tensor_pipe": trec.get("tensor_pipe") if trec else None,
                          "kernel": top + "_tc_kernel", "flops_per_launch": fl,
                          "flops": "executed MMA flops: three bf16 products, padded tiles",
                          "avg_launch_ms": tt, "peak_source": src},
@@ -1096,7 +1149,7 @@ def run_shared64(args):
             "speedup_vs_fp32_per_gather": round(res["fp32_per_gather"]["ms_per_pair"] /
                                                 tc["ms_per_pair"], 3),
             "err_sample": {"gathers": sample_g, "traces": len(traces), "slices": slices}}
-    print(json.dumps(line), flush=True)
+    return line
 
 
 if __name__ == "__main__":

@@ -62,3 +62,19 @@ def test_tc_flops_hand_count():
     assert adj == nbins * chunks * 1 * 4 * k * 128 * 2 * gp
     with pytest.raises(Exception):
         bench.tc_flops(hx, hy[:-1], nq, ntheta, nbins, G)
+
+
+def test_gpu_dot_rel_helper_on_cpu_matrices():
+    """The dot-test helper behind the shared-geometry arms' dot_test_rel: an
+    exact transpose pair gives rounding-level values, a pair whose adjoint is
+    off by one entry does not (run here on CPU tensors)."""
+    import torch
+    rng = np.random.default_rng(7)
+    A = torch.from_numpy(rng.standard_normal((300, 200)).astype(np.float32))
+    m = torch.from_numpy(rng.standard_normal(200).astype(np.float32))
+    exact = bench.gpu_dot_rel(lambda x: A @ x, lambda y: A.T @ y, m, 3)
+    assert exact < 1e-6
+    B = A.clone()
+    B[10, 20] += 1.0
+    off = bench.gpu_dot_rel(lambda x: A @ x, lambda y: B.T @ y, m, 3)
+    assert off > 1e-4
