@@ -19,7 +19,7 @@
 // address, so the address of each device is cached and every plan creation
 // refreshes it (after a cudaDeviceReset, old plans are invalid anyway and a
 // new plan brings a valid address).  The transform call itself therefore
-// neither loads a module nor commits memory, and can follow a stream capture.
+// neither loads a module nor commits memory.
 // All calls share the array and it keeps the last call's contents; the work
 // counter is cleared on every call and the spectra are fully overwritten.
 // Calls whose kernels overlap on the GPU (different streams without
