@@ -78,3 +78,22 @@ def test_gpu_dot_rel_helper_on_cpu_matrices():
     B[10, 20] += 1.0
     off = bench.gpu_dot_rel(lambda x: A @ x, lambda y: B.T @ y, m, 3)
     assert off > 1e-4
+
+
+def test_traffic_record_follows_the_source_hash(tmp_path, monkeypatch):
+    """A committed ncu record is reported only while the files that define
+    its kernel hash to the recorded value: editing one of them hides it."""
+    import hashlib
+    import json
+    src = tmp_path / "k.cu"
+    src.write_text("__global__ void k() {}\n")
+    (tmp_path / "profiles").mkdir()
+    rec = {"kernel": "k", "dram_bytes": 123, "files": ["k.cu"],
+           "sha256": hashlib.sha256(src.read_bytes()).hexdigest()}
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps({"kernels": {"st": rec}}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.traffic_record("st")["dram_bytes"] == 123
+    assert bench.traffic_record("other") is None
+    src.write_text("__global__ void k() { }\n")
+    assert bench.traffic_record("st") is None
+
