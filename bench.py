@@ -991,11 +991,26 @@ def measure_shared64(args, rank, steps):
     ds = {i: x.astype(np.float32) for i, x in zip(sample_g, dl)}
     check = rank == 0 and not args.no_cpu_baseline
     ref = {}
+    full = None                 # the FP64 checker's whole pair of gather fg
+    fg = sample_g[0]
+    cpu = None
     if check:
         import oracle
         from oracle import ops
         op = oracle.make_plan(**geo.geom_kwargs())
-        for i in sample_g:
+        # one whole forward+adjoint pair of one gather: the CPU baseline, and
+        # the reference of every arm's error on that whole gather
+        t0 = time.perf_counter()
+        full = (ops.forward(op, ms[fg].astype(np.float64)),
+                ops.adjoint(op, ds[fg].astype(np.float64)))
+        el = time.perf_counter() - t0
+        cpu = {"value": round(1.0 / el, 5), "unit": "gather-pairs/s", "cores": ops.threads(),
+               "kind": "oracle",
+               "sample": f"1 forward+adjoint pair of one of the {G} gathers (all "
+                         f"{geo.ntr} traces, {geo.nq} q x {geo.ntheta} azimuths), FP64, "
+                         f"{el:.1f} s wall"}
+        ref[fg] = (full[0][:, traces], full[1][:, :, slices])
+        for i in sample_g[1:]:
             ref[i] = (ops.forward_traces(op, ms[i].astype(np.float64), traces),
                       ops.adjoint_slices(op, ds[i].astype(np.float64), slices))
 
@@ -1063,8 +1078,11 @@ def measure_shared64(args, rank, steps):
                 else:
                     dgi = do.view(G, geo.nt, geo.ntr)[i]
                     mgi = mo.view((G,) + shape_m)[i]
-                err[i] = (rel(dgi.cpu().numpy()[:, traces].astype(np.float64), ref[i][0]),
-                          rel(mgi.cpu().numpy()[:, :, slices].astype(np.float64), ref[i][1]))
+                dgh = dgi.cpu().numpy().astype(np.float64)
+                mgh = mgi.cpu().numpy().astype(np.float64)
+                err[i] = (rel(dgh[:, traces], ref[i][0]), rel(mgh[:, :, slices], ref[i][1]))
+                if i == fg:
+                    err_full = (rel(dgh, full[0]), rel(mgh, full[1]))
         res[prec] = {"ms_per_pair": round(ms_pair, 3),
                      "gather_pairs_per_s": round(G / (ms_pair / 1e3), 2),
                      "stages_ms": {L.STAGE_NAMES[i]: round(t[i] / n[i], 3)
@@ -1076,7 +1094,9 @@ def measure_shared64(args, rank, steps):
         if err:
             res[prec]["err_vs_fp64"] = {
                 "forward_rel_l2_max": max(e[0] for e in err.values()),
-                "adjoint_rel_l2_max": max(e[1] for e in err.values())}
+                "adjoint_rel_l2_max": max(e[1] for e in err.values()),
+                "whole_gather": {"gather": fg, "forward_rel_l2": err_full[0],
+                                 "adjoint_rel_l2": err_full[1]}}
         del gp, m, d, mo, do
         torch.cuda.empty_cache()
 
@@ -1099,8 +1119,11 @@ def measure_shared64(args, rank, steps):
         for i in sample_g:
             dg = g1.forward(torch.from_numpy(ms[i].ravel()).cuda()).cpu().numpy()
             mg = g1.adjoint(torch.from_numpy(ds[i].ravel()).cuda()).cpu().numpy()
-            err1[i] = (rel(dg.reshape(geo.nt, geo.ntr)[:, traces].astype(np.float64), ref[i][0]),
-                       rel(mg.reshape(shape_m)[:, :, slices].astype(np.float64), ref[i][1]))
+            dgh = dg.reshape(geo.nt, geo.ntr).astype(np.float64)
+            mgh = mg.reshape(shape_m).astype(np.float64)
+            err1[i] = (rel(dgh[:, traces], ref[i][0]), rel(mgh[:, :, slices], ref[i][1]))
+            if i == fg:
+                err1_full = (rel(dgh, full[0]), rel(mgh, full[1]))
     res["fp32_per_gather"] = {"ms_per_pair": round(ms1, 3),
                               "gather_pairs_per_s": round(G / (ms1 / 1e3), 2),
                               "dot_test_rel": gpu_dot_rel(g1.forward, g1.adjoint, m1[0], 11),
@@ -1109,7 +1132,9 @@ def measure_shared64(args, rank, steps):
     if err1:
         res["fp32_per_gather"]["err_vs_fp64"] = {
             "forward_rel_l2_max": max(e[0] for e in err1.values()),
-            "adjoint_rel_l2_max": max(e[1] for e in err1.values())}
+            "adjoint_rel_l2_max": max(e[1] for e in err1.values()),
+            "whole_gather": {"gather": fg, "forward_rel_l2": err1_full[0],
+                             "adjoint_rel_l2": err1_full[1]}}
     del g1, m1, d1, mo1, do1
     torch.cuda.empty_cache()
 
@@ -1148,7 +1173,10 @@ def measure_shared64(args, rank, steps):
             "speedup_vs_fp32": round(res["fp32"]["ms_per_pair"] / tc["ms_per_pair"], 3),
             "speedup_vs_fp32_per_gather": round(res["fp32_per_gather"]["ms_per_pair"] /
                                                 tc["ms_per_pair"], 3),
-            "err_sample": {"gathers": sample_g, "traces": len(traces), "slices": slices}}
+            "err_sample": {"gathers": sample_g, "traces": len(traces), "slices": slices,
+                           "whole_gather": fg}}
+    if cpu:
+        line["cpu_baseline"] = cpu
     return line
 
 
